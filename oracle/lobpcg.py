@@ -1,0 +1,172 @@
+"""Block LOBPCG with soft locking, B = I, no constraints.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+Follows the algorithm of Section 2.2 ("The Detailed Description of the LOBPCG
+Algorithm", steps 1-33) with B = I (so BX = X, BW = W, BP = P and 6m vectors
+are stored, as the paper notes after the algorithm) and no constraint block Y
+(steps 2 and 10 are empty).  Soft locking as in Section 2.3: only the active
+columns J get residuals, preconditioned residuals and directions; all m
+columns of X stay in the Rayleigh-Ritz basis.
+
+Readings of points the paper leaves open (each listed in the design notes):
+* convergence test (step 8): column j leaves J when ||A x_j - lambda_j x_j||_2
+  <= tol * |lambda_j| (``tol_mode="relative"``, default) or <= tol
+  (``"absolute"``, the paper's literal wording); J only shrinks.
+* loop bound (step 6, k = 0..MaxIterations): the pass k = maxit performs only
+  steps 7-8; ``iters`` is the k at which J became empty.
+* Gram blocks (steps 18-22): computed explicitly, including the diagonal blocks
+  the paper sets to Lambda and I, and symmetrised (G + G^T)/2 (the MATLAB
+  variant the paper reports as more accurate).  ``gram="paper"`` sets them as
+  printed in the algorithm.
+* Cholesky (steps 3, 11, 14): scale-invariant via unit-diagonal scaling.
+* breakdown: if chol(P_J^T P_J) or the Rayleigh-Ritz with P fails, the P block
+  is dropped for that iteration (k = 0 form of steps 21-22 and 30-32); if
+  chol(X^T X) or chol(W_J^T W_J) fails the solve stops with status "breakdown".
+* at exit every residual is recomputed from A X (not the implicitly updated AX).
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import laplace
+from .dense import Breakdown, scaled_cholesky, apply_inverse_upper, symmetrize, rayleigh_ritz
+
+
+@dataclass
+class Result:
+    lam: np.ndarray
+    X: np.ndarray
+    iters: int
+    status: str                     # "converged" | "not_converged" | "breakdown" | "nonfinite"
+    resid: np.ndarray               # final ||A x_j - lambda_j x_j||, from A X
+    history: list = field(default_factory=list)
+
+
+class Laplace7:
+    """The operator A as a callable on (n, m) blocks."""
+
+    def __init__(self, dims, scale=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.scale = laplace.default_scale(self.dims) if scale is None else float(scale)
+        self.n = laplace.npoints(self.dims)
+
+    def __call__(self, U):
+        return laplace.apply(U, self.dims, self.scale)
+
+
+def _converged(norm, lam, tol, tol_mode):
+    bound = tol * abs(lam) if tol_mode == "relative" else tol
+    return norm <= bound
+
+
+def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False):
+    """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity)."""
+    X = np.array(X0, dtype=np.float64, copy=True)
+    n, m = X.shape
+    hist = []
+    if not np.all(np.isfinite(X)):
+        return Result(np.full(m, np.nan), X, 0, "nonfinite", np.full(m, np.nan))
+    precond = (lambda R: R) if T is None else T
+
+    # Step 3: orthonormalise X (B = I): R = chol(X^T X), X = X R^-1, AX = A X.
+    try:
+        R = scaled_cholesky(X.T @ X)
+    except Breakdown:
+        return Result(np.full(m, np.nan), X, 0, "breakdown", np.full(m, np.nan))
+    X = apply_inverse_upper(X, R)
+    AX = A(X)
+    # Step 4: initial Ritz vectors from (X^T AX) TMP = TMP Lambda.
+    lam, TMP = rayleigh_ritz(symmetrize(X.T @ AX), np.eye(m), m)
+    X = X @ TMP
+    AX = AX @ TMP
+    # Step 5: all columns active.
+    J = list(range(m))
+    P = AP = None
+    iters, status = maxit, "not_converged"
+
+    for k in range(0, maxit + 1):
+        # Step 7: residuals of the active columns.
+        W = AX[:, J] - X[:, J] * lam[J][None, :]
+        norms = np.linalg.norm(W, axis=0)
+        if not (np.all(np.isfinite(norms)) and np.all(np.isfinite(lam))):
+            status, iters = "nonfinite", k
+            break
+        # Step 8: soft-lock converged columns; exit when none is left.
+        keep = [t for t, j in enumerate(J) if not _converged(norms[t], lam[j], tol, tol_mode)]
+        if record:
+            hist.append(dict(k=k, lam=lam.copy(), J=list(J), norms=norms.copy(),
+                             orth=float(np.max(np.abs(X.T @ X - np.eye(m)))), dropped_p=False))
+        J = [J[t] for t in keep]
+        W = W[:, keep]
+        if not J:
+            status, iters = "converged", k
+            break
+        if k == maxit:
+            break
+        # Step 9: precondition.
+        W = precond(W)
+        # Step 11: orthonormalise W_J.
+        try:
+            R = scaled_cholesky(W.T @ W)
+        except Breakdown:
+            status, iters = "breakdown", k
+            break
+        W = apply_inverse_upper(W, R)
+        # Step 12: AW_J = A W_J.
+        AW = A(W)
+        # Steps 13-16: orthonormalise P_J and update AP_J (k > 0).
+        use_p = k > 0
+        if use_p:
+            PJ, APJ = P[:, J], AP[:, J]
+            try:
+                R = scaled_cholesky(PJ.T @ PJ)
+                PJ = apply_inverse_upper(PJ, R)
+                APJ = apply_inverse_upper(APJ, R)
+            except Breakdown:
+                use_p = False
+        # Steps 17-24: Gram matrices and the Rayleigh-Ritz eigenproblem.
+        dropped = False
+        while True:
+            S = [X, W] + ([PJ] if use_p else [])
+            AS = [AX, AW] + ([APJ] if use_p else [])
+            Sm, ASm = np.hstack(S), np.hstack(AS)
+            gramA = symmetrize(Sm.T @ ASm)
+            gramB = symmetrize(Sm.T @ Sm)
+            if gram == "paper":
+                gramA[:m, :m] = np.diag(lam)
+                off = 0
+                for blk in S:
+                    w = blk.shape[1]
+                    gramB[off:off + w, off:off + w] = np.eye(w)
+                    off += w
+            try:
+                lam, C = rayleigh_ritz(gramA, gramB, m)
+                break
+            except Breakdown:
+                if use_p:
+                    use_p, dropped = False, True
+                    continue
+                status, iters = "breakdown", k
+                lam = None
+                break
+        if lam is None:
+            lam = hist[-1]["lam"] if hist else np.full(m, np.nan)
+            break
+        if record and dropped:
+            hist[-1]["dropped_p"] = True
+        # Steps 25-33: Ritz vectors.
+        b = len(J)
+        CX, CW = C[:m], C[m:m + b]
+        P = W @ CW
+        AP = AW @ CW
+        if use_p:
+            CP = C[m + b:m + 2 * b]
+            P = P + PJ @ CP
+            AP = AP + APJ @ CP
+        X = X @ CX + P
+        AX = AX @ CX + AP
+
+    resid = np.linalg.norm(A(X) - X * lam[None, :], axis=0)
+    return Result(lam, X, iters, status, resid, hist)
