@@ -1,0 +1,228 @@
+/*
+ * lobpcg_gb300.h -- C ABI of the GB300 (sm_103a) LOBPCG eigensolver.
+ *
+ * Computes the m smallest eigenpairs of the 7-point finite-difference 3-D
+ * Laplacian with Dirichlet boundaries by the block Locally Optimal
+ * Preconditioned Conjugate Gradient method of Knyazev, Argentati, Lashuk and
+ * Ovtchinnikov, "Block Locally Optimal Preconditioned Eigenvalue Xolvers
+ * (BLOPEX) in hypre and PETSc": the algorithm of Section 2.2 with B = I, no
+ * constraints and the soft locking of Section 2.3, preconditioned by a
+ * geometric-multigrid V-cycle that stands in for the paper's hypre/PETSc
+ * preconditioners.  Every step of an iteration runs in this library's own
+ * CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: a status code (LOBPCG_OK = 0, LOBPCG_NOT_CONVERGED = 1,
+ *    negative = error).  The library never aborts, exits or traps.  A CUDA
+ *    error poisons the handle: afterwards every call except lobpcg_destroy
+ *    and lobpcg_last_error returns LOBPCG_ERR_CUDA.
+ *  - Blocks of vectors are column-major: column j of an n-by-m block starts at
+ *    ptr + j*ld (ld >= n, in elements).  Grid point (i, j, k) of an
+ *    nx x ny x nz interior grid (0-based) has row index p = i + nx*(j + ny*k).
+ *  - "device" pointers are CUDA device (or managed) memory on the handle's
+ *    device; "host" pointers are ordinary host memory.  Input pointers are
+ *    borrowed for the duration of the call only; output buffers belong to the
+ *    caller.  The handle owns all of its workspace.
+ *  - All device work is enqueued on the handle's stream.  Entry points that
+ *    return host-visible results synchronise that stream before returning.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef LOBPCG_GB300_H
+#define LOBPCG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LOBPCG_OK              0
+#define LOBPCG_NOT_CONVERGED   1   /* maxit reached; outputs are valid      */
+#define LOBPCG_ERR_ARG        -1   /* invalid argument                      */
+#define LOBPCG_ERR_OOM        -2   /* the allocator returned NULL           */
+#define LOBPCG_ERR_CUDA       -3   /* CUDA error; the handle is poisoned    */
+#define LOBPCG_ERR_BREAKDOWN  -4   /* Gram matrix of X or W_J not positive definite */
+#define LOBPCG_ERR_NONFINITE  -5   /* NaN or Inf in the iterates            */
+#define LOBPCG_ERR_STATE      -6   /* call out of order                     */
+#define LOBPCG_ERR_TIMEOUT    -7   /* reserved: no kernel of this library waits */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define LOBPCG_FP64            0   /* every step in float64                 */
+#define LOBPCG_MIXED           1   /* reserved for the mixed-precision form */
+
+#define LOBPCG_LAPLACE7        0   /* constant-coefficient 7-point stencil  */
+
+#define LOBPCG_PRECOND_NONE    0   /* T = I                                 */
+#define LOBPCG_PRECOND_GMG     1   /* geometric-multigrid V-cycle           */
+
+#define LOBPCG_TOL_RELATIVE    0   /* ||A x_j - l_j x_j|| <= tol * |l_j|    */
+#define LOBPCG_TOL_ABSOLUTE    1   /* ||A x_j - l_j x_j|| <= tol            */
+
+#define LOBPCG_GRAM_EXPLICIT   0   /* all Gram blocks computed, symmetrised */
+#define LOBPCG_GRAM_PAPER      1   /* Lambda / I diagonal blocks (steps 18-22 as printed) */
+
+#define LOBPCG_MAX_M          32   /* largest block size m                  */
+#define LOBPCG_NPHASES         8
+
+/* Phase indices of lobpcg_info.phase_ms. */
+#define LOBPCG_PH_RESIDUAL     0   /* steps 7-8  */
+#define LOBPCG_PH_PRECOND      1   /* step 9     */
+#define LOBPCG_PH_CHOLQR_W     2   /* step 11    */
+#define LOBPCG_PH_SPMV         3   /* step 12    */
+#define LOBPCG_PH_CHOLQR_P     4   /* steps 13-16 */
+#define LOBPCG_PH_GRAM         5   /* steps 17-23 */
+#define LOBPCG_PH_RR           6   /* step 24    */
+#define LOBPCG_PH_UPDATE       7   /* steps 25-33 */
+
+typedef struct lobpcg_handle lobpcg_t;
+
+/* Device-memory allocator.  alloc returns device memory usable on `stream`
+ * (a cudaStream_t) or NULL; free releases it.  With a NULL allocator the
+ * library uses cudaMallocAsync / cudaFreeAsync on the handle's stream. */
+typedef struct lobpcg_allocator {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void  (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} lobpcg_allocator;
+
+/* Result summary of a solve. */
+typedef struct lobpcg_info {
+    int32_t status;          /* same value as the return code                     */
+    int32_t iters;           /* iterations performed (k at which J became empty)  */
+    int32_t active;          /* |J| at exit                                       */
+    int32_t p_dropped;       /* iterations in which the P block was dropped       */
+    double  max_rel_resid;   /* max_j ||A x_j - l_j x_j|| / |l_j|, from A X at exit */
+    double  setup_ms;        /* device time of steps 1-5                           */
+    double  solve_ms;        /* device time of the iteration loop                  */
+    double  phase_ms[LOBPCG_NPHASES];  /* device time per phase, summed over iterations;
+                                          filled only when phase timing is enabled */
+} lobpcg_info;
+
+/* ---- solver-level entry points ------------------------------------------ */
+
+/* Create a handle on CUDA device `device`.  `stream` is a cudaStream_t (NULL =
+ * the legacy default stream); `alloc` may be NULL; `precision` is LOBPCG_FP64.
+ * On success *h receives the handle.  Errors: ERR_ARG, ERR_CUDA. */
+int lobpcg_create(lobpcg_t** h, int device, void* stream,
+                  const lobpcg_allocator* alloc, int precision);
+
+/* Set the operator A (Section 4, model problem): (A u)_p = scale * (6 u_p -
+ * sum of the six neighbours of p), neighbours outside the grid are zero.
+ * kind = LOBPCG_LAPLACE7; nx, ny, nz >= 1; scale > 0 (h^-2 = (n+1)^2 for the
+ * unit cube; 1.0 gives the unscaled spectrum of Section 4.1).  `kappa_faces`
+ * is reserved and must be NULL.  Resets the preconditioner.  Errors: ERR_ARG. */
+int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz,
+                        double scale, const double* kappa_faces);
+
+/* Set the preconditioner T (Algorithm step 9; Section 2.1.1 requires T linear,
+ * symmetric, positive definite).  kind = LOBPCG_PRECOND_NONE or _GMG.  For GMG:
+ * `levels` >= 1 grid levels, level l+1 having floor(n/2) points per axis;
+ * nu_pre = nu_post >= 1 weighted-Jacobi sweeps with weight omega in (0, 1];
+ * full-weighting restriction R = P^T/8, trilinear prolongation P, rediscretised
+ * coarse operators (scale / 4 per level) and an exact dense solve on the
+ * coarsest level (at most 4096 points).  Must follow lobpcg_set_operator.
+ * Errors: ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA. */
+int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre,
+                              int nu_post, double omega);
+
+/* Options: tolerance mode (LOBPCG_TOL_*), Gram variant (LOBPCG_GRAM_*), and
+ * per-phase device timing (0/1; adds event records inside each iteration). */
+int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timing);
+
+/* Supply the initial block X0 (Algorithm input X): n-by-m, column-major, leading
+ * dimension ldx, copied into the handle.  on_host = 1: X0 is host memory;
+ * 0: device memory.  Used by the next lobpcg_solve / lobpcg_begin with the same
+ * m instead of the seeded random block.  Errors: ERR_ARG, ERR_STATE, ERR_CUDA. */
+int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on_host);
+
+/* Solve: steps 1-5, then iterations k = 0..maxit of steps 7-33 until every
+ * column satisfies the tolerance (the pass k = maxit performs only steps 7-8).
+ * Without lobpcg_set_initial, X0 is the seeded SplitMix64 block: entry
+ * (p, j) = 2 * (out[p + n j] >> 11) * 2^-53 - 1, out = outputs of SplitMix64
+ * started at state `seed`.  1 <= m <= LOBPCG_MAX_M, m <= n/2; tol >= 0;
+ * maxit >= 0.  `out` may be NULL.  Returns OK, NOT_CONVERGED, ERR_BREAKDOWN,
+ * ERR_NONFINITE, ERR_ARG, ERR_STATE, ERR_OOM or ERR_CUDA.  After OK or
+ * NOT_CONVERGED (and after BREAKDOWN / NONFINITE, with the last valid
+ * iterate) lobpcg_get_eigenpairs returns the result. */
+int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed,
+                 lobpcg_info* out);
+
+/* Step-wise form of lobpcg_solve.  lobpcg_begin performs steps 1-5;
+ * lobpcg_iterate then performs up to `steps` passes of steps 7-33 and returns
+ * OK once J is empty (NOT_CONVERGED while columns remain active).  A tol of 0
+ * keeps every column active (fixed work per pass).  lobpcg_finish recomputes
+ * the residuals from A X (as lobpcg_solve does at exit). */
+int lobpcg_begin(lobpcg_t* h, int m, double tol, uint64_t seed);
+int lobpcg_iterate(lobpcg_t* h, int steps, lobpcg_info* out);
+int lobpcg_finish(lobpcg_t* h, lobpcg_info* out);
+
+/* Copy out the result: lambda (host, m values ascending), X (n-by-m,
+ * column-major, leading dimension ldx; host if x_on_host else device; may be
+ * NULL) and resid (host, m values of ||A x_j - lambda_j x_j||_2 from A X; may
+ * be NULL).  Errors: ERR_STATE (nothing solved yet), ERR_ARG, ERR_CUDA. */
+int lobpcg_get_eigenpairs(lobpcg_t* h, double* lambda, double* X, int64_t ldx,
+                          int x_on_host, double* resid);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle.  h may be NULL (returns the last lobpcg_create error). */
+const char* lobpcg_last_error(const lobpcg_t* h);
+
+/* Release the handle and all of its workspace.  NULL is accepted. */
+int lobpcg_destroy(lobpcg_t* h);
+
+/* ---- kernel-level entry points -------------------------------------------
+ * Each applies one step of the iteration to caller-owned device buffers, on
+ * the handle's stream, using the handle's operator and preconditioner.  They
+ * exist so that every kernel can be checked on its own and reused. */
+
+/* X0 generator (Algorithm input; SplitMix64 as in lobpcg_solve): writes the
+ * n-by-m block with n = the operator's point count into device X. */
+int lobpcg_op_random_block(lobpcg_t* h, uint64_t seed, int m, double* X, int64_t ldx);
+
+/* Y = A X for `ncols` columns (Algorithm steps 3 and 12): device X, Y, which
+ * must not overlap. */
+int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx,
+                      double* Y, int64_t ldy);
+
+/* E = T R for `ncols` columns (Algorithm step 9; T = I copies): device R, E,
+ * which must not overlap. */
+int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,
+                      double* E, int64_t lde);
+
+/* Column residuals (Algorithm step 7): for t < ncols, j = cols[t] (host array),
+ * W[:, t] = AX[:, j] - lambda[j] X[:, j] (lambda: device, m values) and
+ * norms[t] = ||W[:, t]||_2 (host output).  W may be NULL (norms only). */
+int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X,
+                       const double* AX, int64_t ld, const double* lambda,
+                       double* W, int64_t ldw, double* norms);
+
+/* Gram matrices (Algorithm steps 17-23): S = [S0 S1 S2] with widths w0, w1, w2
+ * (w1, w2 may be 0), each block n rows with leading dimension ld; AS likewise.
+ * Writes the q-by-q (q = w0 + w1 + w2) column-major device matrices
+ * gramA = (S^T AS + AS^T S)/2 and gramB = S^T S.  AS0 may be NULL (gramA skipped).
+ * Deterministic: partial sums per thread block are added in a fixed order. */
+int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double* S2,
+                   const double* AS0, const double* AS1, const double* AS2,
+                   int64_t ld, int w0, int w1, int w2, double* gramA, double* gramB);
+
+/* Cholesky orthonormalisation (Algorithm steps 3, 11, 14-15): G = V^T V,
+ * R = chol(G) computed on the unit-diagonal scaling of G, V <- V R^-1 and, if
+ * AV != NULL, AV <- AV R^-1 (in place, device, b columns, leading dimension ld).
+ * Returns ERR_BREAKDOWN (buffers untouched) if a pivot of the scaled factor is
+ * <= b * 2^-52. */
+int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld);
+
+/* Rayleigh-Ritz (Algorithm step 24) on device matrices: gramA C = gramB C Lambda
+ * for q-by-q symmetric gramA, gramB (column-major), the m smallest eigenvalues
+ * ascending into device lambda and the gramB-orthonormal eigenvectors into
+ * device C (q-by-m, column-major, ld q).  q <= 3 * LOBPCG_MAX_M.  Returns
+ * ERR_BREAKDOWN if gramB is not numerically positive definite. */
+int lobpcg_op_rayleigh_ritz(lobpcg_t* h, int q, int m, const double* gramA,
+                            const double* gramB, double* lambda, double* C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOBPCG_GB300_H */

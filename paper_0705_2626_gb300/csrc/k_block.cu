@@ -1,0 +1,386 @@
+// Tall-skinny block kernels of one LOBPCG iteration (B = I):
+//   random initial block (Algorithm input X, SplitMix64 counter generator),
+//   residuals and their norms (steps 7-8),
+//   Gram matrices [X W_J P_J]^T [AX AW_J AP_J] and [X W_J P_J]^T [X W_J P_J] (steps 17-23,
+//   and the Cholesky Gram matrices of steps 3, 11, 14),
+//   multiplication by the inverse Cholesky factor (steps 3, 11, 14-15),
+//   the Ritz update of P, AP, X, AX (steps 25-33).
+// Reductions over the n grid points are deterministic: per-thread-block partial sums land
+// in scratch memory and are added in a fixed order by a second kernel, so repeated runs are
+// bit-identical.
+#include "common.cuh"
+
+namespace lg {
+namespace {
+
+// ------------------------------------------------------------------ SplitMix64
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_random_block(uint64_t seed, int64_t n, int m, double* __restrict__ X, int64_t ldx) {
+    const int64_t total = n * m;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / n, p = t - j * n;
+        const uint64_t z = splitmix64_out(seed, (uint64_t)t);
+        X[j * ldx + p] = (double)(z >> 11) * 0x1p-52 - 1.0;   // 2 * (z >> 11) * 2^-53 - 1, exact
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the thread block in a fixed order; result valid in thread 0.
+__device__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+constexpr int kResThreads = 256;
+
+__global__ void __launch_bounds__(kResThreads)
+    k_residual(int64_t n, int64_t rows_per_chunk, ColList cols, const double* __restrict__ X,
+               const double* __restrict__ AX, int64_t ld, const double* __restrict__ lam,
+               double* __restrict__ W, int64_t ldw, double* __restrict__ partial, int nchunks) {
+    __shared__ double red[32];
+    const int t = blockIdx.y;
+    const int j = cols.idx[t];
+    const double lj = lam[j];
+    const int64_t r0 = blockIdx.x * rows_per_chunk;
+    const int64_t r1 = min(n, r0 + rows_per_chunk);
+    const double* xc = X + (int64_t)j * ld;
+    const double* ac = AX + (int64_t)j * ld;
+    double* wc = W ? W + (int64_t)t * ldw : nullptr;
+    double acc = 0.0;
+    for (int64_t p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
+        const double w = fma(-lj, __ldg(xc + p), __ldg(ac + p));
+        if (wc) wc[p] = w;
+        acc = fma(w, w, acc);
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[(int64_t)t * nchunks + blockIdx.x] = s;
+}
+
+__global__ void k_norms_finalize(int nchunks, const double* __restrict__ partial,
+                                 double* __restrict__ norms) {
+    const int t = blockIdx.x;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < nchunks; c += 32) s += partial[(int64_t)t * nchunks + c];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) norms[t] = sqrt(s);
+}
+
+// ------------------------------------------------------------------ Gram
+constexpr int kGK = 16;   // grid points per shared-memory stage
+constexpr int kTM = 4;    // each thread owns a kTM x kTM tile of the output
+
+__device__ __forceinline__ const double* col_ptr(const Blocks3& B, int c) {
+    if (c < B.w[0]) return B.p[0] + (int64_t)c * B.ld;
+    c -= B.w[0];
+    if (c < B.w[1]) return B.p[1] + (int64_t)c * B.ld;
+    c -= B.w[1];
+    return B.p[2] + (int64_t)c * B.ld;
+}
+
+// Partial sums of S^T AS (all q x q entries, "A") and S^T S (upper tiles, "B") over one row
+// range per thread block.  Output tile (ti, tj) of the A part uses S columns of row tile ti and
+// AS columns of column tile tj; tiles are numbered row-major so that the threads of a warp
+// share ti (broadcast shared-memory reads of S) and walk along tj.
+__global__ void __launch_bounds__(1024)
+    k_gram(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
+                       double* __restrict__ part) {
+    extern __shared__ double sm[];
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    const int ldsm = T * kTM + 1;                 // odd row length: conflict-free stores
+    double* sS = sm;                              // [kGK][ldsm]
+    double* sA = sm + kGK * ldsm;                 // [kGK][ldsm]
+    const int ntA = with_a ? T * T : 0;
+    const int ntB = T * (T + 1) / 2;
+    const int tile = threadIdx.x;
+    const bool active = tile < ntA + ntB;
+    const bool isA = tile < ntA;
+    int ti = 0, tj = 0;
+    if (isA) {
+        ti = tile / T;
+        tj = tile - ti * T;
+    } else if (active) {
+        int u = tile - ntA;                       // upper tiles ti <= tj, row-major
+        ti = 0;
+        while (u >= T - ti) { u -= T - ti; ++ti; }
+        tj = ti + u;
+    }
+    double acc[kTM][kTM];
+#pragma unroll
+    for (int a = 0; a < kTM; ++a)
+#pragma unroll
+        for (int b = 0; b < kTM; ++b) acc[a][b] = 0.0;
+
+    const int64_t r0 = blockIdx.x * rows_per_part;
+    const int64_t r1 = min(n, r0 + rows_per_part);
+    const double* rhs = isA ? sA : sS;
+    for (int64_t base = r0; base < r1; base += kGK) {
+        for (int e = threadIdx.x; e < kGK * T * kTM; e += blockDim.x) {
+            const int c = e / kGK, k = e - c * kGK;
+            const int64_t p = base + k;
+            double vs = 0.0, va = 0.0;
+            if (c < q && p < r1) {
+                vs = __ldg(col_ptr(S, c) + p);
+                if (with_a) va = __ldg(col_ptr(AS, c) + p);
+            }
+            sS[k * ldsm + c] = vs;
+            if (with_a) sA[k * ldsm + c] = va;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int k = 0; k < kGK; ++k) {
+                double a[kTM], b[kTM];
+#pragma unroll
+                for (int u = 0; u < kTM; ++u) {
+                    a[u] = sS[k * ldsm + ti * kTM + u];
+                    b[u] = rhs[k * ldsm + tj * kTM + u];
+                }
+#pragma unroll
+                for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                    for (int v = 0; v < kTM; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    double* out = part + (int64_t)blockIdx.x * 2 * q * q + (isA ? 0 : (int64_t)q * q);
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v) {
+            const int i = ti * kTM + u, j = tj * kTM + v;
+            if (i < q && j < q) out[i + (int64_t)q * j] = acc[u][v];
+        }
+}
+
+// One warp per unordered pair (i <= j): fixed-order sums of the partials.
+__global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ part, int with_a,
+                                double* __restrict__ gA, double* __restrict__ gB,
+                                const double* __restrict__ paper_lam, int w0, int w1, int w2) {
+    const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = (int64_t)q * (q + 1) / 2;
+    if (pair >= npairs) return;
+    int j = 0;
+    int64_t u = pair;
+    while (u >= j + 1) { u -= j + 1; ++j; }       // column j, row i <= j
+    const int i = (int)u;
+    const int64_t q2 = (int64_t)q * q;
+    double sb = 0.0, sa1 = 0.0, sa2 = 0.0;
+    for (int c = lane; c < nparts; c += 32) {
+        const double* P = part + (int64_t)c * 2 * q2;
+        sb += P[q2 + i + (int64_t)q * j];
+        if (with_a) {
+            sa1 += P[i + (int64_t)q * j];
+            sa2 += P[j + (int64_t)q * i];
+        }
+    }
+    sb = warp_sum(sb);
+    sa1 = warp_sum(sa1);
+    sa2 = warp_sum(sa2);
+    if (lane) return;
+    double a = 0.5 * (sa1 + sa2);
+    double b = sb;
+    if (paper_lam) {
+        auto blk = [&](int c) { return c < w0 ? 0 : (c < w0 + w1 ? 1 : 2); };
+        if (i < w0 && j < w0) a = (i == j) ? paper_lam[i] : 0.0;
+        if (blk(i) == blk(j)) b = (i == j) ? 1.0 : 0.0;
+    }
+    if (with_a) { gA[i + (int64_t)q * j] = a; gA[j + (int64_t)q * i] = a; }
+    gB[i + (int64_t)q * j] = b;
+    gB[j + (int64_t)q * i] = b;
+}
+
+// ------------------------------------------------------------------ Ritz update
+constexpr int kCG = 4;   // output columns per thread
+
+__global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__ C,
+                         double* Xout, double* Pout, int64_t ldout,
+                         const unsigned* __restrict__ status, unsigned skip) {
+    extern __shared__ double sC[];                 // q x m, column-major
+    if (status && (*status & skip)) return;
+    const int q = S.q();
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < q * m; e += 32 * blockDim.y) sC[e] = C[e];
+    __syncthreads();
+    const int c0 = threadIdx.y * kCG;
+    const int w0 = S.w[0], w1 = S.w[1], w2 = S.w[2];
+    const int64_t ld = S.ld;
+    for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
+        const int64_t p = base + threadIdx.x;
+        const bool valid = p < n;
+        double accP[kCG], accX[kCG];
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) accP[c] = accX[c] = 0.0;
+        if (valid) {
+            for (int i = 0; i < w1; ++i) {
+                const double v = S.p[1][(int64_t)i * ld + p];
+#pragma unroll
+                for (int c = 0; c < kCG; ++c) accP[c] = fma(v, sC[(w0 + i) + q * min(c0 + c, m - 1)], accP[c]);
+            }
+            for (int i = 0; i < w2; ++i) {
+                const double v = S.p[2][(int64_t)i * ld + p];
+#pragma unroll
+                for (int c = 0; c < kCG; ++c)
+                    accP[c] = fma(v, sC[(w0 + w1 + i) + q * min(c0 + c, m - 1)], accP[c]);
+            }
+            for (int i = 0; i < w0; ++i) {
+                const double v = S.p[0][(int64_t)i * ld + p];
+#pragma unroll
+                for (int c = 0; c < kCG; ++c) accX[c] = fma(v, sC[i + q * min(c0 + c, m - 1)], accX[c]);
+            }
+        }
+        __syncthreads();   // every input row of this tile is read before any output is written
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < kCG; ++c) {
+                if (c0 + c < m) {
+                    Pout[(int64_t)(c0 + c) * ldout + p] = accP[c];
+                    Xout[(int64_t)(c0 + c) * ldout + p] = accX[c] + accP[c];
+                }
+            }
+        }
+    }
+}
+
+// V <- V Rinv with Rinv upper triangular (b x b, column-major): each thread owns one grid point
+// and kCG output columns c0..c0+kCG-1, so it needs input columns 0..c0+kCG-1 only.
+__global__ void k_apply_upper(int64_t n, int b, const double* Vin, int64_t ldin, double* Vout,
+                              int64_t ldout, const double* __restrict__ Rinv,
+                              const unsigned* __restrict__ status, unsigned skip) {
+    extern __shared__ double sR[];
+    if (status && (*status & skip)) return;
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < b * b; e += 32 * blockDim.y) sR[e] = Rinv[e];
+    __syncthreads();
+    const int c0 = threadIdx.y * kCG;
+    const int iend = min(b, c0 + kCG);
+    for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
+        const int64_t p = base + threadIdx.x;
+        const bool valid = p < n;
+        double acc[kCG];
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) acc[c] = 0.0;
+        if (valid) {
+            for (int i = 0; i < iend; ++i) {
+                const double v = Vin[(int64_t)i * ldin + p];
+#pragma unroll
+                for (int c = 0; c < kCG; ++c) acc[c] = fma(v, sR[i + b * min(c0 + c, b - 1)], acc[c]);
+            }
+        }
+        __syncthreads();   // in place: all inputs of this tile are read before any write
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < kCG; ++c)
+                if (c0 + c < b) Vout[(int64_t)(c0 + c) * ldout + p] = acc[c];
+        }
+    }
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+void launch_random_block(uint64_t seed, int64_t n, int m, double* X, int64_t ldx, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(n * m, 256), (int64_t)kNumSMs * 16);
+    k_random_block<<<(unsigned)blocks, 256, 0, st>>>(seed, n, m, X, ldx);
+    LG_CHECK_LAUNCH();
+}
+
+int residual_chunks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8 * kResThreads), 2 * kNumSMs));
+}
+
+void launch_residual(int64_t n, const ColList& cols, const double* X, const double* AX, int64_t ld,
+                     const double* lambda, double* W, int64_t ldw, double* partial, cudaStream_t st) {
+    if (cols.n <= 0) return;
+    const int nchunks = residual_chunks(n);
+    const int64_t rows = ceil_div(n, nchunks);
+    dim3 grid((unsigned)nchunks, (unsigned)cols.n);
+    k_residual<<<grid, kResThreads, 0, st>>>(n, rows, cols, X, AX, ld, lambda, W, ldw, partial,
+                                             nchunks);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_norms_finalize(int ncols, int nchunks, const double* partial, double* norms,
+                           cudaStream_t st) {
+    if (ncols <= 0) return;
+    k_norms_finalize<<<ncols, 32, 0, st>>>(nchunks, partial, norms);
+    LG_CHECK_LAUNCH();
+}
+
+int gram_parts(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 64 * kGK), 2 * kNumSMs));
+}
+
+int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n) * 2 * q * q; }
+
+void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
+                 cudaStream_t st) {
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    const int ntiles = (AS ? T * T : 0) + T * (T + 1) / 2;
+    const int threads = (int)std::max<int64_t>(64, ceil_div(ntiles, 32) * 32);
+    LG_REQUIRE(threads <= 1024, LOBPCG_ERR_ARG, "Gram basis too wide");
+    const size_t smem = 2 * kGK * (size_t)(T * kTM + 1) * sizeof(double);
+    const int64_t rows = ceil_div(n, nparts);
+    Blocks3 A = AS ? *AS : S;
+    k_gram<<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, double* gramA,
+                          double* gramB, const double* paper_lambda, const Blocks3* widths,
+                          cudaStream_t st) {
+    const int64_t npairs = (int64_t)q * (q + 1) / 2;
+    const int64_t threads = npairs * 32;
+    const int w0 = widths ? widths->w[0] : q, w1 = widths ? widths->w[1] : 0,
+              w2 = widths ? widths->w[2] : 0;
+    k_gram_finalize<<<(unsigned)ceil_div(threads, 256), 256, 0, st>>>(
+        q, nparts, part, with_a ? 1 : 0, gramA, gramB, paper_lambda, w0, w1, w2);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_apply_rinv(int64_t n, int b, const double* Vin, int64_t ldin, double* Vout,
+                       int64_t ldout, const double* Rinv, const unsigned* status,
+                       unsigned skip_mask, cudaStream_t st) {
+    if (b <= 0) return;
+    const int groups = (int)ceil_div(b, kCG);
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
+    k_apply_upper<<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(double), st>>>(
+        n, b, Vin, ldin, Vout, ldout, Rinv, status, skip_mask);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout, double* Pout,
+                   int64_t ldout, const unsigned* status, unsigned skip_mask, cudaStream_t st) {
+    const int groups = (int)ceil_div(m, kCG);
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
+    const size_t smem = (size_t)S.q() * m * sizeof(double);
+    k_update<<<(unsigned)blocks, dim3(32, groups), smem, st>>>(n, m, S, C, Xout, Pout, ldout, status,
+                                                               skip_mask);
+    LG_CHECK_LAUNCH();
+}
+
+}  // namespace lg

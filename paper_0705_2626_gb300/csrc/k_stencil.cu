@@ -1,0 +1,269 @@
+// Stencil-family kernels: the block 7-point SpMV (Algorithm steps 3 and 12) and the
+// kernels of the multigrid V-cycle that serves as the preconditioner T (step 9).
+//
+// All of them are one generic structured sweep
+//     y = a*x + b*(sum of the six neighbours of x) [+ c*z]          (zero outside the grid)
+// which covers
+//     SpMV            y = A x            a = 6s,              b = -s
+//     Jacobi sweep    e' = e + w D^-1 (r - A e)
+//                        = (1-w) e + (w/6) nb(e) + (w/(6s)) r        (D = 6s)
+//     first sweep     from e = 0 the first two sweeps fold into one:
+//                     e2 = alpha(2-w) r + (alpha w/6) nb(r),   alpha = w/(6s)
+//     residual        res = r - A e = -6s e + s nb(e) + r
+// Layout: column-major blocks, point p = i + nx*(j + ny*k).  Each thread owns one (i, j)
+// line and marches along k over a chunk of planes, carrying the k-1, k, k+1 values in
+// registers; in-plane neighbours come through L1.  In float64 the sweep is bound by the
+// FP64 pipe (7-8 FP64 instructions per point), not by HBM.
+#include "common.cuh"
+
+namespace lg {
+namespace {
+
+constexpr int kTX = 32, kTY = 4;
+
+__host__ __device__ inline int zchunk_for(int nz) { return nz >= 64 ? 16 : (nz >= 16 ? 8 : nz); }
+
+template <bool HAS_Z>
+__global__ void __launch_bounds__(kTX* kTY)
+    k_stencil_axpby(Grid3 g, int zchunk, int nzc, double a, double b, const double* __restrict__ x,
+                    int64_t ldx, double c, const double* __restrict__ z, int64_t ldz,
+                    double* __restrict__ y, int64_t ldy) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / nzc;
+    const int kc = blockIdx.z - col * nzc;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = kc * zchunk;
+    const int k1 = min(k0 + zchunk, g.nz);
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const double* xc = x + (int64_t)col * ldx;
+    const double* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
+    double* yc = y + (int64_t)col * ldy;
+    int64_t p = i + sy * (j + (int64_t)g.ny * k0);
+    double xm = (k0 > 0) ? __ldg(xc + p - sz) : 0.0;
+    double x0 = __ldg(xc + p);
+    const bool hasl = i > 0, hasr = i + 1 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
+    for (int k = k0; k < k1; ++k, p += sz) {
+        const double xp = (k + 1 < g.nz) ? __ldg(xc + p + sz) : 0.0;
+        double nb = xm + xp;
+        if (hasl) nb += __ldg(xc + p - 1);
+        if (hasr) nb += __ldg(xc + p + 1);
+        if (hasd) nb += __ldg(xc + p - sy);
+        if (hasu) nb += __ldg(xc + p + sy);
+        double v = fma(b, nb, a * x0);
+        if (HAS_Z) v = fma(c, __ldg(zc + p), v);
+        yc[p] = v;
+        xm = x0;
+        x0 = xp;
+    }
+}
+
+// Full weighting: coarse point (I, J, K) (0-based) sits on fine (2I+1, 2J+1, 2K+1);
+// weights 1, 1/2 per axis for offsets 0, +-1, overall factor 1/8 (R = P^T / 8).
+__global__ void __launch_bounds__(kTX* kTY)
+    k_restrict(Grid3 gf, Grid3 gc, const double* __restrict__ rf, int64_t ldf,
+               double* __restrict__ rc, int64_t ldc) {
+    const int I = blockIdx.x * kTX + threadIdx.x;
+    const int J = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / gc.nz;
+    const int K = blockIdx.z - col * gc.nz;
+    if (I >= gc.nx || J >= gc.ny) return;
+    const double* f = rf + (int64_t)col * ldf;
+    const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
+    double s = 0.0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int kk = fk + dz;
+        if (kk >= gf.nz) continue;
+        const double wz = dz == 0 ? 1.0 : 0.5;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int jj = fj + dy;
+            if (jj >= gf.ny) continue;
+            const double wzy = wz * (dy == 0 ? 1.0 : 0.5);
+            const int64_t row = (int64_t)gf.nx * (jj + (int64_t)gf.ny * kk);
+            double t = __ldg(f + row + fi);
+            if (fi - 1 >= 0) t = fma(0.5, __ldg(f + row + fi - 1), t);
+            if (fi + 1 < gf.nx) t = fma(0.5, __ldg(f + row + fi + 1), t);
+            s = fma(wzy, t, s);
+        }
+    }
+    rc[(int64_t)col * ldc + I + (int64_t)gc.nx * (J + (int64_t)gc.ny * K)] = 0.125 * s;
+}
+
+// Trilinear prolongation: fine index f (1-based) takes coarse f/2 with weight 1 when f is
+// even, coarse (f-1)/2 and (f+1)/2 with weight 1/2 each when f is odd; coarse indices 0
+// and nc+1 are boundary zeros.
+struct Taps {
+    int idx[2];
+    double w[2];
+    int n;
+};
+__device__ inline Taps taps1d(int f0, int nc) {
+    Taps t;
+    const int f = f0 + 1;
+    t.n = 0;
+    if ((f & 1) == 0) {
+        const int I = f >> 1;
+        if (I <= nc) { t.idx[t.n] = I - 1; t.w[t.n] = 1.0; ++t.n; }
+    } else {
+        const int I1 = (f - 1) >> 1, I2 = (f + 1) >> 1;
+        if (I1 >= 1) { t.idx[t.n] = I1 - 1; t.w[t.n] = 0.5; ++t.n; }
+        if (I2 <= nc) { t.idx[t.n] = I2 - 1; t.w[t.n] = 0.5; ++t.n; }
+    }
+    return t;
+}
+
+__global__ void __launch_bounds__(kTX* kTY)
+    k_prolong_add(Grid3 gf, Grid3 gc, const double* __restrict__ ec, int64_t ldc,
+                  double* __restrict__ ef, int64_t ldf) {
+    const int i = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / gf.nz;
+    const int k = blockIdx.z - col * gf.nz;
+    if (i >= gf.nx || j >= gf.ny) return;
+    const double* c = ec + (int64_t)col * ldc;
+    const Taps tx = taps1d(i, gc.nx), ty = taps1d(j, gc.ny), tz = taps1d(k, gc.nz);
+    double s = 0.0;
+    for (int a = 0; a < tz.n; ++a)
+        for (int b = 0; b < ty.n; ++b) {
+            const double w = tz.w[a] * ty.w[b];
+            const int64_t row = (int64_t)gc.nx * (ty.idx[b] + (int64_t)gc.ny * tz.idx[a]);
+            for (int d = 0; d < tx.n; ++d) s = fma(w * tx.w[d], __ldg(c + row + tx.idx[d]), s);
+        }
+    const int64_t p = (int64_t)col * ldf + i + (int64_t)gf.nx * (j + (int64_t)gf.ny * k);
+    ef[p] += s;
+}
+
+// Coarsest-level exact solve.  The 7-point Dirichlet operator s*(6u - nb) on an
+// nx x ny x nz box has the orthonormal eigenvectors Qz (x) Qy (x) Qx with
+// Q_d[a][i] = sqrt(2/(n_d+1)) sin(pi (a+1)(i+1)/(n_d+1)) (symmetric, Q_d^2 = I) and the
+// eigenvalues 4s (sin^2(pi(a+1)/(2(nx+1))) + ...), so A^-1 = Q diag(1/lambda) Q.
+__global__ void k_coarse_setup(Grid3 g, double scale, double* tab) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    double* Qx = tab;
+    double* Qy = Qx + nx * nx;
+    double* Qz = Qy + ny * ny;
+    double* lam = Qz + nz * nz;
+    const int64_t total = (int64_t)nx * nx + ny * ny + nz * nz + g.n();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < (int64_t)nx * nx) {
+            const int a = t / nx, i = t % nx;
+            Qx[t] = sqrt(2.0 / (nx + 1)) * sinpi((double)((a + 1) * (i + 1)) / (nx + 1));
+        } else if (t < (int64_t)nx * nx + ny * ny) {
+            const int u = t - nx * nx, a = u / ny, i = u % ny;
+            Qy[u] = sqrt(2.0 / (ny + 1)) * sinpi((double)((a + 1) * (i + 1)) / (ny + 1));
+        } else if (t < (int64_t)nx * nx + ny * ny + nz * nz) {
+            const int u = t - nx * nx - ny * ny, a = u / nz, i = u % nz;
+            Qz[u] = sqrt(2.0 / (nz + 1)) * sinpi((double)((a + 1) * (i + 1)) / (nz + 1));
+        } else {
+            const int64_t p = t - (int64_t)nx * nx - ny * ny - nz * nz;
+            const int a = p % nx, b = (p / nx) % ny, c = p / ((int64_t)nx * ny);
+            const double sx = sinpi((double)(a + 1) / (2.0 * (nx + 1)));
+            const double sy = sinpi((double)(b + 1) / (2.0 * (ny + 1)));
+            const double sz = sinpi((double)(c + 1) / (2.0 * (nz + 1)));
+            lam[p] = 4.0 * scale * (sx * sx + sy * sy + sz * sz);
+        }
+    }
+}
+
+// One 1-D transform pass along axis `ax` (0 = x, 1 = y, 2 = z): out = Q_ax applied to in.
+__device__ void sine_pass(const Grid3& g, int ax, const double* __restrict__ Q,
+                          const double* in, double* out) {
+    const int n = g.nx * g.ny * g.nz;
+    const int na = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+    const int stride = ax == 0 ? 1 : (ax == 1 ? g.nx : g.nx * g.ny);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int a = (p / stride) % na;           // output index along the axis
+        const int base = p - a * stride;
+        double s = 0.0;
+        for (int i = 0; i < na; ++i) s = fma(__ldg(Q + a * na + i), in[base + i * stride], s);
+        out[p] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const double* __restrict__ r,
+                               int64_t ldr, double* __restrict__ e, int64_t lde) {
+    extern __shared__ double sm[];
+    const int n = g.nx * g.ny * g.nz;
+    double* u = sm;
+    double* v = sm + n;
+    const double* Qx = tab;
+    const double* Qy = Qx + g.nx * g.nx;
+    const double* Qz = Qy + g.ny * g.ny;
+    const double* lam = Qz + g.nz * g.nz;
+    const int col = blockIdx.x;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) u[p] = r[(int64_t)col * ldr + p];
+    __syncthreads();
+    sine_pass(g, 0, Qx, u, v);
+    sine_pass(g, 1, Qy, v, u);
+    sine_pass(g, 2, Qz, u, v);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) v[p] /= lam[p];
+    __syncthreads();
+    sine_pass(g, 0, Qx, v, u);
+    sine_pass(g, 1, Qy, u, v);
+    sine_pass(g, 2, Qz, v, u);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) e[(int64_t)col * lde + p] = u[p];
+}
+
+}  // namespace
+
+void launch_stencil_axpby(const Grid3& g, int ncols, double a, double b, const double* x,
+                          int64_t ldx, double c, const double* z, int64_t ldz, double* y,
+                          int64_t ldy, cudaStream_t st) {
+    if (ncols <= 0 || g.n() == 0) return;
+    const int zc = zchunk_for(g.nz);
+    const int nzc = (int)ceil_div(g.nz, zc);
+    dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
+    dim3 block(kTX, kTY);
+    if (z)
+        k_stencil_axpby<true><<<grid, block, 0, st>>>(g, zc, nzc, a, b, x, ldx, c, z, ldz, y, ldy);
+    else
+        k_stencil_axpby<false><<<grid, block, 0, st>>>(g, zc, nzc, a, b, x, ldx, 0.0, nullptr, 0, y,
+                                                       ldy);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_restrict(const Grid3& gf, const Grid3& gc, int ncols, const double* rf, int64_t ldf,
+                     double* rc, int64_t ldc, cudaStream_t st) {
+    if (ncols <= 0) return;
+    dim3 grid((unsigned)ceil_div(gc.nx, kTX), (unsigned)ceil_div(gc.ny, kTY), (unsigned)(gc.nz * ncols));
+    k_restrict<<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, rf, ldf, rc, ldc);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_prolong_add(const Grid3& gf, const Grid3& gc, int ncols, const double* ec,
+                        int64_t ldc, double* ef, int64_t ldf, cudaStream_t st) {
+    if (ncols <= 0) return;
+    dim3 grid((unsigned)ceil_div(gf.nx, kTX), (unsigned)ceil_div(gf.ny, kTY), (unsigned)(gf.nz * ncols));
+    k_prolong_add<<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, ec, ldc, ef, ldf);
+    LG_CHECK_LAUNCH();
+}
+
+int64_t coarse_tables_size(const Grid3& g) {
+    return (int64_t)g.nx * g.nx + (int64_t)g.ny * g.ny + (int64_t)g.nz * g.nz + g.n();
+}
+
+void launch_coarse_setup(const Grid3& g, double scale, double* tables, cudaStream_t st) {
+    const int64_t total = coarse_tables_size(g);
+    k_coarse_setup<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(g, scale, tables);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_coarse_solve(const Grid3& g, int ncols, const double* tables, const double* r,
+                         int64_t ldr, double* e, int64_t lde, cudaStream_t st) {
+    if (ncols <= 0) return;
+    const size_t smem = 2 * (size_t)g.n() * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        LG_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * 4096 * (int)sizeof(double)));
+        attr_set = true;
+    }
+    k_coarse_solve<<<ncols, 256, smem, st>>>(g, tables, r, ldr, e, lde);
+    LG_CHECK_LAUNCH();
+}
+
+}  // namespace lg

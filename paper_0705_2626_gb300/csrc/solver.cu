@@ -1,0 +1,912 @@
+// LOBPCG driver and the C ABI declared in include/lobpcg_gb300.h.
+//
+// One handle = one operator (7-point Laplacian on an nx x ny x nz grid), one preconditioner
+// (V-cycle hierarchy or identity) and the workspace of a block of m vectors.  The iteration
+// follows Section 2.2 of the BLOPEX paper (steps 1-33) with B = I (6m stored vectors), no
+// constraints and the soft locking of Section 2.3.  Every step runs in this library's kernels;
+// the host only keeps the active index set J, which needs the b residual norms of each
+// iteration (one device-to-host copy per iteration, together with a status word that the small
+// dense kernels use to report breakdowns).  Nothing on the iteration path falls back to the CPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace lg;
+
+namespace {
+
+struct DBuf {
+    double* p = nullptr;
+    size_t bytes = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lobpcg_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lobpcg_allocator alloc{};
+    bool has_alloc = false;
+    int precision = LOBPCG_FP64;
+    std::string err;
+    bool poisoned = false;
+
+    // operator
+    bool has_op = false;
+    Grid3 g{0, 0, 0};
+    double scale = 1.0;
+    // preconditioner
+    int pc_kind = LOBPCG_PRECOND_NONE;
+    int levels = 1, nu_pre = 2, nu_post = 2;
+    double omega = 2.0 / 3.0;
+    std::vector<Grid3> lv;
+    std::vector<double> lscale;
+    DBuf coarse_tab;
+    // options
+    int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
+
+    // workspace for a block of wm columns
+    int wm = 0;
+    int64_t ld = 0;
+    DBuf X, AX, W, AW, P, AP, Pc, APc, E0, T0;
+    std::vector<DBuf> lr, le, lt;
+    std::vector<int64_t> lld;
+    DBuf part;          // Gram / residual partial sums
+    DBuf small;         // gramA, gramB, C, lam, Rinv, norms, rr work
+    unsigned* status = nullptr;
+    size_t part_doubles = 0;
+    double *gramA = nullptr, *gramB = nullptr, *Cm = nullptr, *lam = nullptr, *Rinv = nullptr,
+           *norms = nullptr, *rrwork = nullptr, *Gsmall = nullptr;
+
+    // user initial block
+    DBuf X0;
+    int X0_m = 0;
+
+    // solve state
+    int state = 0;      // 0 none, 1 iterating, 2 finished
+    int m = 0;
+    double tol = 0.0;
+    int k = 0;
+    bool pending_check = false;
+    std::vector<int> J;
+    std::vector<double> lam_h, norms_h, resid_h;
+    int p_dropped = 0;
+    double setup_ms = 0.0, solve_ms = 0.0;
+    double phase_ms[LOBPCG_NPHASES] = {};
+    cudaEvent_t ev[LOBPCG_NPHASES + 2] = {};
+    int last_status = LOBPCG_OK;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ memory
+void* dalloc(lobpcg_t* h, size_t bytes) {
+    if (bytes == 0) return nullptr;
+    void* p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->stream);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, h->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (!p) throw Error(LOBPCG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    return p;
+}
+
+void dfree(lobpcg_t* h, DBuf& b) {
+    if (b.p) {
+        if (h->has_alloc) h->alloc.free(h->alloc.ctx, b.p, b.bytes, (void*)h->stream);
+        else cudaFreeAsync(b.p, h->stream);
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void ensure(lobpcg_t* h, DBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return;
+    dfree(h, b);
+    b.p = (double*)dalloc(h, bytes);
+    b.bytes = bytes;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+void free_workspace(lobpcg_t* h) {
+    for (DBuf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0,
+                    &h->part, &h->small})
+        dfree(h, *b);
+    for (auto& b : h->lr) dfree(h, b);
+    for (auto& b : h->le) dfree(h, b);
+    for (auto& b : h->lt) dfree(h, b);
+    h->lr.clear();
+    h->le.clear();
+    h->lt.clear();
+    h->wm = 0;
+    h->status = nullptr;
+}
+
+// Workspace for blocks of up to wm columns (6m vectors of the algorithm + V-cycle buffers).
+void ensure_workspace(lobpcg_t* h, int wm) {
+    if (h->wm >= wm && h->X.p) return;
+    free_workspace(h);
+    h->state = 0;   // a finished or running solve does not survive a reallocation
+    const int64_t n = h->g.n();
+    h->ld = round_up(n, 32);
+    const size_t blk = (size_t)h->ld * wm * sizeof(double);
+    for (DBuf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0})
+        ensure(h, *b, blk);
+    const int L = (int)h->lv.size();
+    h->lr.assign(L, DBuf{});
+    h->le.assign(L, DBuf{});
+    h->lt.assign(L, DBuf{});
+    h->lld.assign(L, 0);
+    for (int l = 1; l < L; ++l) {
+        h->lld[l] = round_up(h->lv[l].n(), 32);
+        const size_t bytes = (size_t)h->lld[l] * wm * sizeof(double);
+        ensure(h, h->lr[l], bytes);
+        ensure(h, h->le[l], bytes);
+        ensure(h, h->lt[l], bytes);
+    }
+    const int q = 3 * wm;
+    h->part_doubles = (size_t)std::max<int64_t>(gram_scratch_doubles(n, q),
+                                                (int64_t)residual_chunks(n) * wm);
+    ensure(h, h->part, h->part_doubles * sizeof(double));
+    const size_t nsmall = 2 * (size_t)q * q + (size_t)q * wm + wm + (size_t)wm * wm + wm +
+                          (size_t)rr_work_doubles(q) + (size_t)wm * wm + 8;
+    ensure(h, h->small, nsmall * sizeof(double));
+    double* s = h->small.p;
+    h->gramA = s; s += (size_t)q * q;
+    h->gramB = s; s += (size_t)q * q;
+    h->Cm = s; s += (size_t)q * wm;
+    h->lam = s; s += wm;
+    h->Rinv = s; s += (size_t)wm * wm;
+    h->norms = s; s += wm;
+    h->rrwork = s; s += rr_work_doubles(q);
+    h->Gsmall = s; s += (size_t)wm * wm;
+    h->status = (unsigned*)s;
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    h->wm = wm;
+}
+
+void require_op(lobpcg_t* h) {
+    LG_REQUIRE(h->has_op, LOBPCG_ERR_STATE, "no operator set (call lobpcg_set_operator first)");
+}
+
+ColList identity_cols(int b) {
+    ColList c{};
+    c.n = b;
+    for (int i = 0; i < b; ++i) c.idx[i] = i;
+    return c;
+}
+
+// ------------------------------------------------------------------ operator and T
+void spmv(lobpcg_t* h, int ncols, const double* x, int64_t ldx, double* y, int64_t ldy) {
+    launch_stencil_axpby(h->g, ncols, 6.0 * h->scale, -h->scale, x, ldx, 0.0, nullptr, 0, y, ldy,
+                         h->stream);
+}
+
+void copy_cols(lobpcg_t* h, int ncols, int64_t n, const double* src, int64_t lds, double* dst,
+               int64_t ldd) {
+    LG_CUDA(cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double),
+                              n * sizeof(double), ncols, cudaMemcpyDeviceToDevice, h->stream));
+}
+
+// V-cycle on level l: e = T_l r for b columns.  tmp is a scratch block of the same shape.
+void vcycle(lobpcg_t* h, int l, int b, const double* r, int64_t ldr, double* e, int64_t lde,
+            double* tmp, int64_t ldt) {
+    const Grid3& g = h->lv[l];
+    const int L = (int)h->lv.size();
+    const int64_t n = g.n();
+    if (l == L - 1) {
+        launch_coarse_solve(g, b, h->coarse_tab.p, r, ldr, e, lde, h->stream);
+        return;
+    }
+    const double s = h->lscale[l], w = h->omega, alpha = w / (6.0 * s);
+    double* cur = e;
+    int64_t ldc = lde;
+    double* oth = tmp;
+    int64_t ldo = ldt;
+    auto swap_bufs = [&]() { std::swap(cur, oth); std::swap(ldc, ldo); };
+    // pre-smoothing from e = 0; the first sweep (e = alpha r) folds into the second
+    int done = 0;
+    if (h->nu_pre >= 2) {
+        launch_stencil_axpby(g, b, alpha * (2.0 - w), alpha * w / 6.0, r, ldr, 0.0, nullptr, 0, cur,
+                             ldc, h->stream);
+        done = 2;
+    } else {
+        launch_stencil_axpby(g, b, alpha, 0.0, r, ldr, 0.0, nullptr, 0, cur, ldc, h->stream);
+        done = 1;
+    }
+    for (; done < h->nu_pre; ++done) {
+        launch_stencil_axpby(g, b, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
+        swap_bufs();
+    }
+    // residual r - A e, restricted to level l+1
+    launch_stencil_axpby(g, b, -6.0 * s, s, cur, ldc, 1.0, r, ldr, oth, ldo, h->stream);
+    const Grid3& gc = h->lv[l + 1];
+    launch_restrict(g, gc, b, oth, ldo, h->lr[l + 1].p, h->lld[l + 1], h->stream);
+    vcycle(h, l + 1, b, h->lr[l + 1].p, h->lld[l + 1], h->le[l + 1].p, h->lld[l + 1],
+           h->lt[l + 1].p, h->lld[l + 1]);
+    launch_prolong_add(g, gc, b, h->le[l + 1].p, h->lld[l + 1], cur, ldc, h->stream);
+    for (int t = 0; t < h->nu_post; ++t) {
+        launch_stencil_axpby(g, b, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
+        swap_bufs();
+    }
+    if (cur != e) copy_cols(h, b, n, cur, ldc, e, lde);
+}
+
+// e = T r (level 0).  tmp: n-by-b scratch, distinct from r and e.
+void precond(lobpcg_t* h, int b, const double* r, int64_t ldr, double* e, int64_t lde,
+             double* tmp, int64_t ldt) {
+    if (h->pc_kind == LOBPCG_PRECOND_NONE) {
+        copy_cols(h, b, h->g.n(), r, ldr, e, lde);
+        return;
+    }
+    vcycle(h, 0, b, r, ldr, e, lde, tmp, ldt);
+}
+
+// ------------------------------------------------------------------ Gram helpers
+Blocks3 blocks(const double* p0, int w0, const double* p1, int w1, const double* p2, int w2,
+               int64_t ld) {
+    Blocks3 b{};
+    b.p[0] = p0; b.w[0] = w0;
+    b.p[1] = w1 ? p1 : p0; b.w[1] = w1;
+    b.p[2] = w2 ? p2 : p0; b.w[2] = w2;
+    b.ld = ld;
+    return b;
+}
+
+void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* gB,
+          const double* paper_lam) {
+    const int64_t n = h->g.n();
+    const int q = S.q();
+    const int nparts = gram_parts(n);
+    LG_REQUIRE((size_t)nparts * 2 * q * q <= h->part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
+    launch_gram(n, S, AS, h->part.p, nparts, h->stream);
+    launch_gram_finalize(q, nparts, h->part.p, AS != nullptr, gA, gB, paper_lam, &S, h->stream);
+}
+
+// ------------------------------------------------------------------ timing
+struct PhaseTimer {
+    lobpcg_t* h;
+    bool on;
+    explicit PhaseTimer(lobpcg_t* hh) : h(hh), on(hh->phase_timing != 0) {}
+    void mark(int i) {
+        if (on) LG_CUDA(cudaEventRecord(h->ev[i], h->stream));
+    }
+};
+
+void events_create(lobpcg_t* h) {
+    for (auto& e : h->ev)
+        if (!e) LG_CUDA(cudaEventCreate(&e));
+}
+
+// ------------------------------------------------------------------ the iteration
+void residual_into_W(lobpcg_t* h) {
+    // step 7 for the current J: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]], norms to host
+    const int64_t n = h->g.n();
+    ColList cols{};
+    cols.n = (int)h->J.size();
+    for (int t = 0; t < cols.n; ++t) cols.idx[t] = h->J[t];
+    launch_residual(n, cols, h->X.p, h->AX.p, h->ld, h->lam, h->W.p, h->ld, h->part.p, h->stream);
+    launch_norms_finalize(cols.n, residual_chunks(n), h->part.p, h->norms, h->stream);
+}
+
+// Copy the small per-iteration results to the host: norms of J, lambda, status word.
+unsigned fetch_small(lobpcg_t* h) {
+    unsigned st = 0;
+    h->norms_h.resize(h->J.size());
+    if (!h->J.empty())
+        LG_CUDA(cudaMemcpyAsync(h->norms_h.data(), h->norms, h->J.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+    h->lam_h.resize(h->m);
+    LG_CUDA(cudaMemcpyAsync(h->lam_h.data(), h->lam, h->m * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    LG_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    LG_CUDA(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
+    require_op(h);
+    const int64_t n = h->g.n();
+    LG_REQUIRE(m >= 1 && m <= LOBPCG_MAX_M, LOBPCG_ERR_ARG, "m out of range [1, 32]");
+    LG_REQUIRE(2 * (int64_t)m <= n, LOBPCG_ERR_ARG, "m too large for the grid (need m <= n/2)");
+    LG_REQUIRE(tol >= 0.0 && std::isfinite(tol), LOBPCG_ERR_ARG, "tol must be finite and >= 0");
+    ensure_workspace(h, m);
+    events_create(h);
+    h->m = m;
+    h->tol = tol;
+    h->k = 0;
+    h->p_dropped = 0;
+    h->J.clear();
+    std::fill(h->phase_ms, h->phase_ms + LOBPCG_NPHASES, 0.0);
+    h->state = 0;
+    cudaStream_t st = h->stream;
+    LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES], st));
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+    // input block
+    if (h->X0.p && h->X0_m == m) copy_cols(h, m, n, h->X0.p, n, h->X.p, h->ld);
+    else launch_random_block(seed, n, m, h->X.p, h->ld, st);
+    // step 3: X = X R^-1 with R = chol(X^T X); AX = A X
+    const Blocks3 SX = blocks(h->X.p, m, nullptr, 0, nullptr, 0, h->ld);
+    gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr);
+    launch_chol_rinv(m, h->Gsmall, h->Rinv, h->status, ST_X_BREAKDOWN, 0u, st);
+    launch_apply_rinv(n, m, h->X.p, h->ld, h->X.p, h->ld, h->Rinv, h->status,
+                      ST_X_BREAKDOWN, st);
+    spmv(h, m, h->X.p, h->ld, h->AX.p, h->ld);
+    // step 4: (X^T AX) TMP = TMP Lambda; X = X TMP; AX = AX TMP
+    const Blocks3 SAX = blocks(h->AX.p, m, nullptr, 0, nullptr, 0, h->ld);
+    gram(h, SX, &SAX, h->gramA, h->gramB, nullptr);
+    launch_rayleigh_ritz(m, m, m, h->gramA, nullptr, h->lam, h->Cm, h->rrwork, h->status,
+                         ST_X_BREAKDOWN, st);
+    launch_update(n, m, SX, h->Cm, h->X.p, h->P.p, h->ld, h->status, ST_X_BREAKDOWN | ST_RR_BREAKDOWN, st);
+    launch_update(n, m, SAX, h->Cm, h->AX.p, h->AP.p, h->ld, h->status, ST_X_BREAKDOWN | ST_RR_BREAKDOWN, st);
+    // step 5 and step 7 of k = 0
+    h->J.resize(m);
+    for (int j = 0; j < m; ++j) h->J[j] = j;
+    residual_into_W(h);
+    LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], st));
+    const unsigned stw = fetch_small(h);
+    float ms = 0.f;
+    LG_CUDA(cudaEventElapsedTime(&ms, h->ev[LOBPCG_NPHASES], h->ev[LOBPCG_NPHASES + 1]));
+    h->setup_ms = ms;
+    h->solve_ms = 0.0;
+    if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite entry in the initial block");
+    if (stw & (ST_X_BREAKDOWN | ST_RR_BREAKDOWN))
+        throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (step 3)");
+    for (double v : h->lam_h)
+        if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value at setup");
+    h->pending_check = true;
+    h->state = 1;
+}
+
+// Steps 7-8 with the norms of the last residual pass: shrink J.  Returns true if J is empty.
+bool check_and_lock(lobpcg_t* h) {
+    if (!h->pending_check) return h->J.empty();
+    h->pending_check = false;
+    for (double v : h->norms_h)
+        if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite residual norm");
+    std::vector<int> keep;   // positions t in the old J that stay active
+    for (size_t t = 0; t < h->J.size(); ++t) {
+        const int j = h->J[t];
+        const double bound = h->tol_mode == LOBPCG_TOL_RELATIVE ? h->tol * std::fabs(h->lam_h[j]) : h->tol;
+        if (!(h->norms_h[t] <= bound)) keep.push_back((int)t);
+    }
+    if (keep.size() != h->J.size()) {
+        // compact the residual block W to the surviving columns
+        std::vector<int> nJ;
+        for (size_t u = 0; u < keep.size(); ++u) {
+            if ((int)u != keep[u])
+                LG_CUDA(cudaMemcpyAsync(h->W.p + (int64_t)u * h->ld, h->W.p + (int64_t)keep[u] * h->ld,
+                                        h->g.n() * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            nJ.push_back(h->J[keep[u]]);
+        }
+        h->J.swap(nJ);
+    }
+    return h->J.empty();
+}
+
+// Steps 9-33 for the current J, then step 7 of the next pass.
+void pass_body(lobpcg_t* h) {
+    const int64_t n = h->g.n();
+    const int m = h->m, b = (int)h->J.size();
+    const int64_t ld = h->ld;
+    cudaStream_t st = h->stream;
+    PhaseTimer tm(h);
+    tm.mark(0);
+    // step 9: W_J = T W_J (output in E0, then the buffers swap roles)
+    precond(h, b, h->W.p, ld, h->E0.p, ld, h->T0.p, ld);
+    std::swap(h->W, h->E0);
+    tm.mark(1);
+    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
+    const Blocks3 SW = blocks(h->W.p, b, nullptr, 0, nullptr, 0, ld);
+    gram(h, SW, nullptr, h->gramA, h->Gsmall, nullptr);
+    launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
+    launch_apply_rinv(n, b, h->W.p, ld, h->W.p, ld, h->Rinv, h->status,
+                      ST_W_BREAKDOWN, st);
+    tm.mark(2);
+    // step 12: AW_J = A W_J
+    spmv(h, b, h->W.p, ld, h->AW.p, ld);
+    tm.mark(3);
+    // steps 13-16: P_J = P_J R^-1, AP_J = AP_J R^-1 with R = chol(P_J^T P_J)
+    const bool use_p = h->k > 0;
+    double* Pj = h->P.p;
+    double* APj = h->AP.p;
+    if (use_p) {
+        if (b != m) {
+            for (int t = 0; t < b; ++t) {
+                LG_CUDA(cudaMemcpyAsync(h->Pc.p + (int64_t)t * ld, h->P.p + (int64_t)h->J[t] * ld,
+                                        n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                LG_CUDA(cudaMemcpyAsync(h->APc.p + (int64_t)t * ld, h->AP.p + (int64_t)h->J[t] * ld,
+                                        n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            Pj = h->Pc.p;
+            APj = h->APc.p;
+        }
+        const Blocks3 SP = blocks(Pj, b, nullptr, 0, nullptr, 0, ld);
+        gram(h, SP, nullptr, h->gramA, h->Gsmall, nullptr);
+        launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
+        launch_apply_rinv(n, b, Pj, ld, Pj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+        launch_apply_rinv(n, b, APj, ld, APj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+    }
+    tm.mark(4);
+    // steps 17-23: Gram matrices of the basis [X W_J P_J]
+    const Blocks3 S = blocks(h->X.p, m, h->W.p, b, Pj, use_p ? b : 0, ld);
+    const Blocks3 AS = blocks(h->AX.p, m, h->AW.p, b, APj, use_p ? b : 0, ld);
+    const int q = S.q();
+    gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
+    tm.mark(5);
+    // step 24: gramA C = gramB C Lambda (P block dropped on device if needed)
+    launch_rayleigh_ritz(q, m + b, m, h->gramA, h->gramB, h->lam, h->Cm, h->rrwork, h->status,
+                         ST_W_BREAKDOWN, st);
+    tm.mark(6);
+    // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
+    const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
+    launch_update(n, m, S, h->Cm, h->X.p, h->P.p, ld, h->status, skip, st);
+    launch_update(n, m, AS, h->Cm, h->AX.p, h->AP.p, ld, h->status, skip, st);
+    tm.mark(7);
+    // step 7 of the next pass
+    residual_into_W(h);
+    const unsigned stw = fetch_small(h);
+    if (h->phase_timing) {
+        // event 0..7 bracket phases 1..7 of this pass; the residual phase is the tail
+        for (int i = 0; i < 7; ++i) {
+            float ms = 0.f;
+            LG_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+            const int ph = i + 1;   // PH_PRECOND .. PH_UPDATE
+            h->phase_ms[ph] += ms;
+        }
+    }
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+    if (stw & ST_P_DROPPED) ++h->p_dropped;
+    if (stw & ST_W_BREAKDOWN)
+        throw Error(LOBPCG_ERR_BREAKDOWN, "W_J^T W_J is not numerically positive definite (step 11)");
+    if (stw & ST_RR_BREAKDOWN)
+        throw Error(LOBPCG_ERR_BREAKDOWN, "gramB is not numerically positive definite (step 24)");
+    if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value");
+    h->k += 1;
+    h->pending_check = true;
+}
+
+// Residuals of all m columns from A X (not the implicitly updated AX); host resid.
+void finish(lobpcg_t* h) {
+    const int64_t n = h->g.n();
+    const int m = h->m;
+    spmv(h, m, h->X.p, h->ld, h->T0.p, h->ld);
+    ColList cols = identity_cols(m);
+    launch_residual(n, cols, h->X.p, h->T0.p, h->ld, h->lam, nullptr, 0, h->part.p, h->stream);
+    launch_norms_finalize(m, residual_chunks(n), h->part.p, h->norms, h->stream);
+    h->resid_h.resize(m);
+    LG_CUDA(cudaMemcpyAsync(h->resid_h.data(), h->norms, m * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    h->lam_h.resize(m);
+    LG_CUDA(cudaMemcpyAsync(h->lam_h.data(), h->lam, m * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    LG_CUDA(cudaStreamSynchronize(h->stream));
+    h->state = 2;
+}
+
+void fill_info(lobpcg_t* h, lobpcg_info* out, int status) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->status = status;
+    out->iters = h->k;
+    out->active = (int)h->J.size();
+    out->p_dropped = h->p_dropped;
+    double mr = 0.0;
+    for (int j = 0; j < (int)h->resid_h.size() && j < (int)h->lam_h.size(); ++j)
+        mr = std::max(mr, h->resid_h[j] / std::fabs(h->lam_h[j]));
+    out->max_rel_resid = mr;
+    out->setup_ms = h->setup_ms;
+    out->solve_ms = h->solve_ms;
+    for (int i = 0; i < LOBPCG_NPHASES; ++i) out->phase_ms[i] = h->phase_ms[i];
+}
+
+// Passes until J is empty or `steps` passes ran.  Returns OK / NOT_CONVERGED.
+int run_passes(lobpcg_t* h, int steps, bool last_is_check_only) {
+    LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES], h->stream));
+    int rc = LOBPCG_NOT_CONVERGED;
+    for (int s = 0; s <= steps; ++s) {
+        if (check_and_lock(h)) { rc = LOBPCG_OK; break; }
+        if (s == steps) break;
+        (void)last_is_check_only;
+        pass_body(h);
+    }
+    LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], h->stream));
+    LG_CUDA(cudaEventSynchronize(h->ev[LOBPCG_NPHASES + 1]));
+    float ms = 0.f;
+    LG_CUDA(cudaEventElapsedTime(&ms, h->ev[LOBPCG_NPHASES], h->ev[LOBPCG_NPHASES + 1]));
+    h->solve_ms += ms;
+    return rc;
+}
+
+// ------------------------------------------------------------------ C-ABI plumbing
+template <class F>
+int guarded(lobpcg_t* h, F&& f) {
+    if (!h) return LOBPCG_ERR_ARG;
+    if (h->poisoned) return LOBPCG_ERR_CUDA;
+    try {
+        LG_CUDA(cudaSetDevice(h->device));
+        h->err.clear();
+        return f();
+    } catch (const Error& e) {
+        h->err = e.what();
+        if (e.code == LOBPCG_ERR_CUDA) h->poisoned = true;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        h->err = "host allocation failed";
+        return LOBPCG_ERR_OOM;
+    } catch (const std::exception& e) {
+        h->err = e.what();
+        return LOBPCG_ERR_ARG;
+    }
+}
+
+bool valid_ld(int64_t ld, int64_t n) { return ld >= n; }
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocator* alloc,
+                  int precision) {
+    if (!out) return LOBPCG_ERR_ARG;
+    *out = nullptr;
+    if (precision != LOBPCG_FP64) {
+        g_create_error = "only LOBPCG_FP64 is available";
+        return LOBPCG_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "invalid CUDA device";
+        return device < 0 ? LOBPCG_ERR_ARG : LOBPCG_ERR_CUDA;
+    }
+    if (alloc && (!alloc->alloc || !alloc->free)) {
+        g_create_error = "allocator needs both alloc and free";
+        return LOBPCG_ERR_ARG;
+    }
+    lobpcg_t* h = new (std::nothrow) lobpcg_t();
+    if (!h) return LOBPCG_ERR_OOM;
+    h->device = device;
+    h->stream = (cudaStream_t)stream;
+    h->precision = precision;
+    if (alloc) {
+        h->alloc = *alloc;
+        h->has_alloc = true;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        g_create_error = "cudaSetDevice failed";
+        return LOBPCG_ERR_CUDA;
+    }
+    g_create_error.clear();
+    *out = h;
+    return LOBPCG_OK;
+}
+
+int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz, double scale,
+                        const double* kappa_faces) {
+    return guarded(h, [&] {
+        LG_REQUIRE(kind == LOBPCG_LAPLACE7, LOBPCG_ERR_ARG, "unknown operator kind");
+        LG_REQUIRE(kappa_faces == nullptr, LOBPCG_ERR_ARG, "kappa_faces must be NULL for LAPLACE7");
+        LG_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1, LOBPCG_ERR_ARG, "grid dimensions must be >= 1");
+        LG_REQUIRE((int64_t)nx * ny * nz <= (int64_t)1 << 31, LOBPCG_ERR_ARG, "grid too large");
+        LG_REQUIRE(scale > 0.0 && std::isfinite(scale), LOBPCG_ERR_ARG, "scale must be > 0");
+        free_workspace(h);
+        dfree(h, h->coarse_tab);
+        dfree(h, h->X0);
+        h->X0_m = 0;
+        h->g = Grid3{nx, ny, nz};
+        h->scale = scale;
+        h->has_op = true;
+        h->pc_kind = LOBPCG_PRECOND_NONE;
+        h->lv.assign(1, h->g);
+        h->lscale.assign(1, scale);
+        h->state = 0;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre, int nu_post,
+                              double omega) {
+    return guarded(h, [&] {
+        require_op(h);
+        LG_REQUIRE(kind == LOBPCG_PRECOND_NONE || kind == LOBPCG_PRECOND_GMG, LOBPCG_ERR_ARG,
+                   "unknown preconditioner kind");
+        free_workspace(h);
+        dfree(h, h->coarse_tab);
+        h->lv.assign(1, h->g);
+        h->lscale.assign(1, h->scale);
+        h->pc_kind = LOBPCG_PRECOND_NONE;
+        if (kind == LOBPCG_PRECOND_NONE) return LOBPCG_OK;
+        LG_REQUIRE(levels >= 1 && levels <= 24, LOBPCG_ERR_ARG, "levels out of range");
+        LG_REQUIRE(nu_pre >= 1 && nu_post == nu_pre, LOBPCG_ERR_ARG,
+                   "need nu_pre == nu_post >= 1 (a symmetric V-cycle)");
+        LG_REQUIRE(omega > 0.0 && omega <= 1.0, LOBPCG_ERR_ARG, "omega must be in (0, 1]");
+        std::vector<Grid3> lv{h->g};
+        std::vector<double> ls{h->scale};
+        for (int l = 1; l < levels; ++l) {
+            const Grid3 p = lv.back();
+            const Grid3 c{p.nx / 2, p.ny / 2, p.nz / 2};
+            LG_REQUIRE(c.nx >= 1 && c.ny >= 1 && c.nz >= 1, LOBPCG_ERR_ARG,
+                       "grid cannot be coarsened to that many levels");
+            lv.push_back(c);
+            ls.push_back(ls.back() / 4.0);
+        }
+        LG_REQUIRE(lv.back().n() <= 4096, LOBPCG_ERR_ARG,
+                   "coarsest level has more than 4096 points; use more levels");
+        h->lv = lv;
+        h->lscale = ls;
+        h->levels = levels;
+        h->nu_pre = nu_pre;
+        h->nu_post = nu_post;
+        h->omega = omega;
+        ensure(h, h->coarse_tab, coarse_tables_size(lv.back()) * sizeof(double));
+        launch_coarse_setup(lv.back(), ls.back(), h->coarse_tab.p, h->stream);
+        h->pc_kind = LOBPCG_PRECOND_GMG;
+        h->state = 0;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timing) {
+    return guarded(h, [&] {
+        LG_REQUIRE(tol_mode == LOBPCG_TOL_RELATIVE || tol_mode == LOBPCG_TOL_ABSOLUTE,
+                   LOBPCG_ERR_ARG, "unknown tolerance mode");
+        LG_REQUIRE(gram_mode == LOBPCG_GRAM_EXPLICIT || gram_mode == LOBPCG_GRAM_PAPER,
+                   LOBPCG_ERR_ARG, "unknown Gram mode");
+        h->tol_mode = tol_mode;
+        h->gram_mode = gram_mode;
+        h->phase_timing = phase_timing ? 1 : 0;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on_host) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(X0 && m >= 1 && m <= LOBPCG_MAX_M && valid_ld(ldx, n), LOBPCG_ERR_ARG,
+                   "invalid initial block");
+        ensure(h, h->X0, (size_t)n * m * sizeof(double));
+        LG_CUDA(cudaMemcpy2DAsync(h->X0.p, n * sizeof(double), X0, ldx * sizeof(double),
+                                  n * sizeof(double), m,
+                                  on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        h->X0_m = m;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
+    return guarded(h, [&] {
+        h->state = 0;
+        begin(h, m, tol, seed);
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_iterate(lobpcg_t* h, int steps, lobpcg_info* out) {
+    int rc = guarded(h, [&] {
+        LG_REQUIRE(h->state == 1, LOBPCG_ERR_STATE, "call lobpcg_begin first");
+        LG_REQUIRE(steps >= 0, LOBPCG_ERR_ARG, "steps must be >= 0");
+        int r = LOBPCG_NOT_CONVERGED;
+        // `steps` passes of steps 7-33, then the check of the pass after them
+        r = run_passes(h, steps, false);
+        return r;
+    });
+    if (h && out) fill_info(h, out, rc);
+    return rc;
+}
+
+int lobpcg_finish(lobpcg_t* h, lobpcg_info* out) {
+    int rc = guarded(h, [&] {
+        LG_REQUIRE(h->state >= 1, LOBPCG_ERR_STATE, "nothing to finish");
+        finish(h);
+        return h->J.empty() ? LOBPCG_OK : LOBPCG_NOT_CONVERGED;
+    });
+    if (h && out) fill_info(h, out, rc);
+    return rc;
+}
+
+int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed, lobpcg_info* out) {
+    int rc = guarded(h, [&] {
+        LG_REQUIRE(maxit >= 0, LOBPCG_ERR_ARG, "maxit must be >= 0");
+        h->state = 0;
+        begin(h, m, tol, seed);
+        int r = LOBPCG_NOT_CONVERGED;
+        try {
+            r = run_passes(h, maxit, true);
+        } catch (const Error& e) {
+            if (e.code == LOBPCG_ERR_CUDA) throw;
+            finish(h);   // last valid iterate stays available
+            throw;
+        }
+        finish(h);
+        return r;
+    });
+    if (h && out) fill_info(h, out, rc);
+    if (h) h->last_status = rc;
+    return rc;
+}
+
+int lobpcg_get_eigenpairs(lobpcg_t* h, double* lambda, double* X, int64_t ldx, int x_on_host,
+                          double* resid) {
+    return guarded(h, [&] {
+        LG_REQUIRE(h->state == 2, LOBPCG_ERR_STATE, "no finished solve on this handle");
+        const int m = h->m;
+        const int64_t n = h->g.n();
+        if (lambda) std::memcpy(lambda, h->lam_h.data(), m * sizeof(double));
+        if (resid) std::memcpy(resid, h->resid_h.data(), m * sizeof(double));
+        if (X) {
+            LG_REQUIRE(valid_ld(ldx, n), LOBPCG_ERR_ARG, "ldx < n");
+            LG_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), h->X.p, h->ld * sizeof(double),
+                                      n * sizeof(double), m,
+                                      x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                      h->stream));
+            LG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        return LOBPCG_OK;
+    });
+}
+
+const char* lobpcg_last_error(const lobpcg_t* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+int lobpcg_destroy(lobpcg_t* h) {
+    if (!h) return LOBPCG_OK;
+    cudaSetDevice(h->device);
+    if (!h->poisoned) {
+        free_workspace(h);
+        dfree(h, h->coarse_tab);
+        dfree(h, h->X0);
+        cudaStreamSynchronize(h->stream);
+        for (auto& e : h->ev)
+            if (e) cudaEventDestroy(e);
+    }
+    cudaGetLastError();
+    delete h;
+    return LOBPCG_OK;
+}
+
+// ---------------------------------------------------------------------- kernel-level ops
+int lobpcg_op_random_block(lobpcg_t* h, uint64_t seed, int m, double* X, int64_t ldx) {
+    return guarded(h, [&] {
+        require_op(h);
+        LG_REQUIRE(X && m >= 1 && valid_ld(ldx, h->g.n()), LOBPCG_ERR_ARG, "invalid block");
+        launch_random_block(seed, h->g.n(), m, X, ldx, h->stream);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx, double* Y, int64_t ldy) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(X && Y && ncols >= 0 && valid_ld(ldx, n) && valid_ld(ldy, n), LOBPCG_ERR_ARG,
+                   "invalid stencil arguments");
+        spmv(h, ncols, X, ldx, Y, ldy);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr, double* E, int64_t lde) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(R && E && ncols >= 1 && ncols <= LOBPCG_MAX_M && valid_ld(ldr, n) &&
+                       valid_ld(lde, n),
+                   LOBPCG_ERR_ARG, "invalid preconditioner arguments");
+        ensure_workspace(h, std::max(h->wm, ncols));
+        precond(h, ncols, R, ldr, E, lde, h->T0.p, h->ld);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X, const double* AX,
+                       int64_t ld, const double* lambda, double* W, int64_t ldw, double* norms) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(ncols >= 1 && ncols <= LOBPCG_MAX_M && cols && X && AX && lambda && norms &&
+                       valid_ld(ld, n) && (!W || valid_ld(ldw, n)),
+                   LOBPCG_ERR_ARG, "invalid residual arguments");
+        ensure_workspace(h, std::max(h->wm, ncols));
+        ColList cl{};
+        cl.n = ncols;
+        for (int t = 0; t < ncols; ++t) cl.idx[t] = cols[t];
+        launch_residual(n, cl, X, AX, ld, lambda, W, ldw, h->part.p, h->stream);
+        launch_norms_finalize(ncols, residual_chunks(n), h->part.p, h->norms, h->stream);
+        LG_CUDA(cudaMemcpyAsync(norms, h->norms, ncols * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double* S2,
+                   const double* AS0, const double* AS1, const double* AS2, int64_t ld, int w0,
+                   int w1, int w2, double* gramA, double* gramB) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        const int q = w0 + w1 + w2;
+        LG_REQUIRE(S0 && gramB && w0 >= 1 && w1 >= 0 && w2 >= 0 && q <= 3 * LOBPCG_MAX_M &&
+                       (w1 == 0 || S1) && (w2 == 0 || S2) && valid_ld(ld, n),
+                   LOBPCG_ERR_ARG, "invalid Gram arguments");
+        LG_REQUIRE(!AS0 || (gramA && (w1 == 0 || AS1) && (w2 == 0 || AS2)), LOBPCG_ERR_ARG,
+                   "invalid Gram arguments (A side)");
+        ensure_workspace(h, std::max(h->wm, (q + 2) / 3));
+        const Blocks3 S = blocks(S0, w0, S1, w1, S2, w2, ld);
+        const Blocks3 AS = blocks(AS0, w0, AS1, w1, AS2, w2, ld);
+        gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(V && b >= 1 && b <= LOBPCG_MAX_M && valid_ld(ld, n), LOBPCG_ERR_ARG,
+                   "invalid CholQR arguments");
+        ensure_workspace(h, std::max(h->wm, b));
+        cudaStream_t st = h->stream;
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        const Blocks3 SV = blocks(V, b, nullptr, 0, nullptr, 0, ld);
+        gram(h, SV, nullptr, h->gramA, h->Gsmall, nullptr);
+        launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
+        launch_apply_rinv(n, b, V, ld, V, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        if (AV) launch_apply_rinv(n, b, AV, ld, AV, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        LG_CUDA(cudaStreamSynchronize(st));
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        if (stw & ST_W_BREAKDOWN) throw Error(LOBPCG_ERR_BREAKDOWN, "Gram matrix not positive definite");
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_rayleigh_ritz(lobpcg_t* h, int q, int m, const double* gramA, const double* gramB,
+                            double* lambda, double* C) {
+    return guarded(h, [&] {
+        require_op(h);
+        LG_REQUIRE(gramA && gramB && lambda && C && q >= 1 && q <= 3 * LOBPCG_MAX_M && m >= 1 &&
+                       m <= q,
+                   LOBPCG_ERR_ARG, "invalid Rayleigh-Ritz arguments");
+        ensure_workspace(h, std::max(h->wm, (q + 2) / 3));
+        cudaStream_t st = h->stream;
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        launch_rayleigh_ritz(q, q, m, gramA, gramB, lambda, C, h->rrwork, h->status, 0u, st);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        LG_CUDA(cudaStreamSynchronize(st));
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        if (stw & ST_RR_BREAKDOWN) throw Error(LOBPCG_ERR_BREAKDOWN, "gramB not positive definite");
+        if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite eigenvalue");
+        return LOBPCG_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+"""Python front end of the GB300 LOBPCG library.
+
+``Solver`` owns one C handle (include/lobpcg_gb300.h).  PyTorch supplies the device memory
+(the handle's workspace comes from torch's caching allocator through the C allocator
+callback) and the CUDA stream; every step of the iteration runs in the CUDA library.
+Blocks of vectors cross the boundary as torch tensors of shape (m, ld): row j of the tensor is
+column j of the column-major n-by-m block.
+"""
+import ctypes
+
+import torch
+
+from . import capi
+
+
+class LobpcgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{capi.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, h=None, allow=(capi.OK,)):
+    if rc not in allow:
+        raise LobpcgError(rc, capi.lobpcg_last_error(h))
+    return rc
+
+
+class _TorchAllocator:
+    """C allocator callbacks backed by torch's caching allocator on one device."""
+
+    def __init__(self, device):
+        self.device = device
+
+        def _alloc(ctx, size, stream):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(size), self.device, int(stream or 0))
+            except Exception:  # the C side maps NULL to LOBPCG_ERR_OOM
+                return None
+
+        def _free(ctx, ptr, size, stream):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._alloc = capi.ALLOC_FN(_alloc)
+        self._free = capi.FREE_FN(_free)
+        self.struct = capi.Allocator(None, self._alloc, self._free)
+
+
+def default_scale(dims):
+    nx, ny, nz = dims
+    return float(nx + 1) ** 2 if nx == ny == nz else 1.0
+
+
+class Solver:
+    """LOBPCG for the m smallest eigenpairs of the 7-point Dirichlet Laplacian on `dims`."""
+
+    def __init__(self, dims, scale=None, precond="gmg", levels=None, nu=2, omega=2.0 / 3.0,
+                 device=0, stream=None, tol_mode="relative", gram="explicit", phase_timing=False,
+                 torch_allocator=True):
+        self.dims = tuple(int(d) for d in dims)
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self.scale = default_scale(self.dims) if scale is None else float(scale)
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = _TorchAllocator(device) if torch_allocator else None
+        h = ctypes.c_void_p()
+        _check(capi.lobpcg_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                  ctypes.byref(self._alloc.struct) if self._alloc else None, capi.FP64))
+        self.h = h
+        _check(capi.lobpcg_set_operator(h, capi.LAPLACE7, *self.dims, self.scale, None), h)
+        if precond == "gmg":
+            if levels is None:
+                levels = 1
+                d = min(self.dims)
+                while d // 2 >= 3 and levels < 24:
+                    d //= 2
+                    levels += 1
+            _check(capi.lobpcg_set_preconditioner(h, capi.PRECOND_GMG, levels, nu, nu, omega), h)
+        elif precond is None or precond == "none":
+            _check(capi.lobpcg_set_preconditioner(h, capi.PRECOND_NONE, 1, 1, 1, 1.0), h)
+        else:
+            raise ValueError(f"unknown preconditioner {precond!r}")
+        self.levels = levels if precond == "gmg" else 1
+        _check(capi.lobpcg_set_options(h, capi.TOL_RELATIVE if tol_mode == "relative" else capi.TOL_ABSOLUTE,
+                                       capi.GRAM_EXPLICIT if gram == "explicit" else capi.GRAM_PAPER,
+                                       1 if phase_timing else 0), h)
+        self.m = None
+        self.info = capi.Info()
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            capi.lobpcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- solving
+    def set_initial(self, X0):
+        """X0: (m, n) float64 tensor (host or device), row j = column j of the block."""
+        X0 = X0.contiguous()
+        on_host = 0 if X0.is_cuda else 1
+        _check(capi.lobpcg_set_initial(self.h, ctypes.c_void_p(X0.data_ptr()), X0.shape[0], X0.shape[1],
+                                       on_host), self.h)
+
+    def solve(self, m, tol=1e-8, maxit=200, seed=2):
+        rc = capi.lobpcg_solve(self.h, m, tol, maxit, seed, ctypes.byref(self.info))
+        self.m = m
+        _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
+        return self.result()
+
+    def begin(self, m, tol=1e-8, seed=2):
+        _check(capi.lobpcg_begin(self.h, m, tol, seed), self.h)
+        self.m = m
+
+    def iterate(self, steps):
+        rc = capi.lobpcg_iterate(self.h, steps, ctypes.byref(self.info))
+        _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
+        return rc
+
+    def finish(self):
+        rc = capi.lobpcg_finish(self.h, ctypes.byref(self.info))
+        _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
+        return rc
+
+    def result(self, with_vectors=True):
+        m = self.m
+        lam = (ctypes.c_double * m)()
+        res = (ctypes.c_double * m)()
+        X = None
+        if with_vectors:
+            X = torch.empty((m, self.n), dtype=torch.float64, device=self.device)
+            torch.cuda.current_stream(self.device).synchronize()
+            _check(capi.lobpcg_get_eigenpairs(self.h, lam, ctypes.c_void_p(X.data_ptr()), self.n, 0, res), self.h)
+        else:
+            _check(capi.lobpcg_get_eigenpairs(self.h, lam, None, self.n, 0, res), self.h)
+        return dict(lam=list(lam), resid=list(res), X=X, iters=self.info.iters, status=self.info.status,
+                    status_name=capi.STATUS_NAMES.get(self.info.status), active=self.info.active,
+                    p_dropped=self.info.p_dropped, setup_ms=self.info.setup_ms, solve_ms=self.info.solve_ms,
+                    max_rel_resid=self.info.max_rel_resid,
+                    phase_ms=dict(zip(capi.PHASE_NAMES, list(self.info.phase_ms))))

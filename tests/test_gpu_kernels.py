@@ -1,0 +1,214 @@
+"""Per-kernel parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances follow from the float64 arithmetic: the two sides sum in different orders, so an
+entry built from k products differs by at most about k * eps times the sum of the magnitudes
+of its terms.  Integer work (the SplitMix64 block) must match bit for bit.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dense, laplace, multigrid, rng  # noqa: E402
+from paper_0705_2626_gb300 import capi  # noqa: E402
+from paper_0705_2626_gb300.solver import Solver  # noqa: E402
+from tests.gpu_util import dev, empty, host, ptr  # noqa: E402
+
+EPS = np.finfo(np.float64).eps
+
+
+def make(dims, scale=1.0, levels=None, precond="gmg"):
+    return Solver(dims, scale=scale, levels=levels, precond=precond)
+
+
+@pytest.mark.parametrize("dims,m,seed", [((7, 9, 5), 3, 2), ((48, 48, 48), 8, 2),
+                                         ((5, 4, 3), 2, 2 ** 64 - 1), ((33, 1, 2), 5, 12345)])
+def test_random_block_bit_exact(dims, m, seed):
+    s = make(dims, precond="none")
+    n = s.n
+    ld = n + 3
+    T = empty(m, ld)
+    assert capi.lobpcg_op_random_block(s.h, seed, m, ptr(T), ld) == capi.OK
+    got = host(T, n)
+    want = rng.uniform_block(seed, n, m)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("dims,m", [((5, 7, 9), 3), ((33, 33, 33), 4), ((1, 1, 7), 2), ((17, 3, 70), 5),
+                                    ((128, 128, 128), 16)])
+def test_stencil_matches_oracle(dims, m):
+    s = make(dims, scale=3.25, precond="none")
+    n = s.n
+    X = np.random.default_rng(1).uniform(-1, 1, (n, m))
+    ld = n + 7
+    Xd, Yd = dev(X, ld), empty(m, ld)
+    assert capi.lobpcg_op_stencil(s.h, m, ptr(Xd), ld, ptr(Yd), ld) == capi.OK
+    got = host(Yd, n)
+    want = laplace.apply(X, dims, 3.25)
+    bound = 16 * EPS * 3.25 * 12 * np.max(np.abs(X))
+    assert np.max(np.abs(got - want)) <= bound
+    assert torch.isnan(Yd[:, n:]).all()          # padding rows untouched
+
+
+@pytest.mark.parametrize("dims,levels,m", [((7, 7, 7), 1, 3), ((8, 8, 8), 2, 2), ((16, 16, 16), 3, 4),
+                                           ((15, 17, 13), 3, 3), ((48, 48, 48), 4, 8),
+                                           ((128, 128, 128), 6, 16)])
+def test_vcycle_matches_oracle(dims, levels, m):
+    scale = laplace.default_scale(dims)
+    s = make(dims, scale=scale, levels=levels)
+    n = s.n
+    R = np.random.default_rng(2).standard_normal((n, m))
+    Rd, Ed = dev(R), empty(m, n)
+    assert capi.lobpcg_op_precond(s.h, m, ptr(Rd), n, ptr(Ed), n) == capi.OK
+    got = host(Ed, n)
+    want = multigrid.VCycle(dims, scale, levels)(R)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_identity_preconditioner_copies():
+    s = make((6, 5, 4), precond="none")
+    R = np.random.default_rng(3).standard_normal((s.n, 3))
+    Rd, Ed = dev(R), empty(3, s.n)
+    assert capi.lobpcg_op_precond(s.h, 3, ptr(Rd), s.n, ptr(Ed), s.n) == capi.OK
+    assert np.array_equal(host(Ed, s.n), R)
+
+
+@pytest.mark.parametrize("dims,m,cols", [((9, 8, 7), 5, [0, 2, 3]), ((64, 64, 64), 16, list(range(16))),
+                                         ((3, 3, 3), 4, [3])])
+def test_residual_and_norms(dims, m, cols):
+    s = make(dims, precond="none")
+    n = s.n
+    g = np.random.default_rng(4)
+    X, AX = g.standard_normal((n, m)), g.standard_normal((n, m))
+    lam = g.uniform(1, 50, m)
+    ld = n + 1
+    Xd, AXd, Wd = dev(X, ld), dev(AX, ld), empty(len(cols), ld)
+    lamd = torch.from_numpy(lam).cuda()
+    norms = (ctypes.c_double * len(cols))()
+    c_cols = (ctypes.c_int * len(cols))(*cols)
+    rc = capi.lobpcg_op_residual(s.h, len(cols), c_cols, ptr(Xd), ptr(AXd), ld, ptr(lamd), ptr(Wd), ld, norms)
+    assert rc == capi.OK
+    W = AX[:, cols] - X[:, cols] * lam[cols][None, :]
+    assert np.max(np.abs(host(Wd, n) - W)) <= 4 * EPS * np.max(np.abs(AX) + np.abs(X) * lam.max())
+    want = np.linalg.norm(W, axis=0)
+    assert np.max(np.abs(np.array(norms[:]) - want) / want) <= 4 * n * EPS
+
+
+@pytest.mark.parametrize("dims,widths", [((33, 33, 33), (8, 5, 5)), ((10, 9, 8), (3, 0, 0)),
+                                         ((16, 16, 16), (4, 4, 0)), ((128, 128, 128), (16, 16, 16)),
+                                         ((20, 20, 20), (32, 32, 32)), ((2, 3, 5), (7, 1, 2))])
+def test_gram_matches_definition(dims, widths):
+    s = make(dims, precond="none")
+    n = s.n
+    q = sum(widths)
+    g = np.random.default_rng(5)
+    S = g.standard_normal((n, q)) * g.uniform(0.1, 10, q)[None, :]
+    AS = g.standard_normal((n, q))
+    ld = n + 2
+    blocks, ablocks, off = [], [], 0
+    for w in widths:
+        blocks.append(dev(S[:, off:off + w], ld) if w else None)
+        ablocks.append(dev(AS[:, off:off + w], ld) if w else None)
+        off += w
+    gA = torch.empty((q, q), dtype=torch.float64, device="cuda")
+    gB = torch.empty((q, q), dtype=torch.float64, device="cuda")
+    rc = capi.lobpcg_op_gram(s.h, *[ptr(b) for b in blocks], *[ptr(b) for b in ablocks], ld, *widths,
+                             ptr(gA), ptr(gB))
+    assert rc == capi.OK
+    # device matrices are column-major: element (i, j) at i + q*j -> transpose of the row-major view
+    GA, GB = gA.cpu().numpy().T, gB.cpu().numpy().T
+    wantA = dense.symmetrize(S.T @ AS)
+    wantB = S.T @ S
+    nrmS, nrmA = np.linalg.norm(S, axis=0), np.linalg.norm(AS, axis=0)
+    boundA = 2 * n * EPS * (np.outer(nrmS, nrmA) + np.outer(nrmA, nrmS)) / 2
+    boundB = 2 * n * EPS * np.outer(nrmS, nrmS)
+    assert np.all(np.abs(GA - wantA) <= boundA)
+    assert np.all(np.abs(GB - wantB) <= boundB)
+    assert np.array_equal(GA, GA.T) and np.array_equal(GB, GB.T)
+
+
+def test_gram_is_deterministic():
+    s = make((40, 40, 40), precond="none")
+    n, q = s.n, 12
+    S = np.random.default_rng(6).standard_normal((n, q))
+    Sd = dev(S)
+    outs = []
+    for _ in range(3):
+        gB = torch.empty((q, q), dtype=torch.float64, device="cuda")
+        assert capi.lobpcg_op_gram(s.h, ptr(Sd), None, None, None, None, None, n, q, 0, 0, None, ptr(gB)) == 0
+        outs.append(gB.cpu().numpy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("dims,b", [((20, 20, 20), 6), ((9, 9, 9), 1), ((32, 32, 32), 32), ((128, 128, 128), 16)])
+def test_cholqr_matches_oracle(dims, b):
+    s = make(dims, precond="none")
+    n = s.n
+    g = np.random.default_rng(7)
+    V = g.standard_normal((n, b)) * np.logspace(-9, 6, b)[None, :]
+    AV = g.standard_normal((n, b))
+    Vd, AVd = dev(V), dev(AV)
+    assert capi.lobpcg_op_cholqr(s.h, b, ptr(Vd), ptr(AVd), n) == capi.OK
+    R = dense.scaled_cholesky(V.T @ V)
+    Q = dense.apply_inverse_upper(V, R)
+    AQ = dense.apply_inverse_upper(AV, R)
+    got, agot = host(Vd, n), host(AVd, n)
+    assert np.max(np.abs(got - Q)) <= 1e-10 * np.max(np.abs(Q))
+    assert np.max(np.abs(agot - AQ)) <= 1e-10 * np.max(np.abs(AQ))
+    assert np.max(np.abs(got.T @ got - np.eye(b))) < 1e-12
+
+
+def test_cholqr_breakdown_leaves_block_untouched():
+    s = make((10, 10, 10), precond="none")
+    V = np.random.default_rng(8).standard_normal((s.n, 4))
+    V[:, 2] = V[:, 0]
+    Vd = dev(V)
+    assert capi.lobpcg_op_cholqr(s.h, 4, ptr(Vd), None, s.n) == capi.ERR_BREAKDOWN
+    assert np.array_equal(host(Vd, s.n), V)
+
+
+def _sym_pair(q, seed, cluster=False):
+    g = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(g.standard_normal((q, q)))
+    ev = np.sort(g.uniform(1, 100, q))
+    if cluster:
+        ev[2:5] = ev[2]
+        ev[7:9] = ev[7] * (1 + 1e-13)
+    A = (Q * ev) @ Q.T
+    Q2, _ = np.linalg.qr(g.standard_normal((q, q)))
+    B = (Q2 * g.uniform(0.5, 2.0, q)) @ Q2.T
+    return 0.5 * (A + A.T), 0.5 * (B + B.T)
+
+
+@pytest.mark.parametrize("q,m,cluster", [(24, 8, False), (48, 16, False), (96, 32, False), (48, 16, True),
+                                         (5, 5, False), (1, 1, False)])
+def test_rayleigh_ritz_matches_oracle(q, m, cluster):
+    s = make((4, 4, 4), precond="none")
+    A, B = _sym_pair(q, q + m, cluster)
+    Ad = torch.from_numpy(A.T.copy()).cuda()
+    Bd = torch.from_numpy(B.T.copy()).cuda()
+    lamd = torch.empty(m, dtype=torch.float64, device="cuda")
+    Cd = torch.empty((m, q), dtype=torch.float64, device="cuda")
+    assert capi.lobpcg_op_rayleigh_ritz(s.h, q, m, ptr(Ad), ptr(Bd), ptr(lamd), ptr(Cd)) == capi.OK
+    lam, C = lamd.cpu().numpy(), Cd.cpu().numpy().T
+    wl, wC = dense.rayleigh_ritz(A, B, m)
+    scale = np.max(np.abs(wl))
+    assert np.max(np.abs(lam - wl)) <= 1e-12 * scale
+    assert np.max(np.abs(C.T @ B @ C - np.eye(m))) <= 1e-12
+    assert np.max(np.abs(A @ C - B @ C * lam[None, :])) <= 1e-11 * scale
+    if not cluster:   # distinct eigenvalues: vectors agree up to sign
+        for j in range(m):
+            assert abs(abs(C[:, j] @ B @ wC[:, j]) - 1.0) < 1e-10
+
+
+def test_rayleigh_ritz_breakdown_on_indefinite_gramB():
+    s = make((4, 4, 4), precond="none")
+    A, B = _sym_pair(12, 3)
+    B[0, 0] = -1.0
+    Ad, Bd = torch.from_numpy(A.T.copy()).cuda(), torch.from_numpy(B.T.copy()).cuda()
+    lamd = torch.empty(4, dtype=torch.float64, device="cuda")
+    Cd = torch.empty((4, 12), dtype=torch.float64, device="cuda")
+    assert capi.lobpcg_op_rayleigh_ritz(s.h, 12, 4, ptr(Ad), ptr(Bd), ptr(lamd), ptr(Cd)) == capi.ERR_BREAKDOWN
