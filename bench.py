@@ -1,0 +1,288 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 LOBPCG hot path.
+
+A step is one LOBPCG iteration (Algorithm steps 7-33 of the BLOPEX paper, Section 2.2: residual,
+V-cycle preconditioner, Cholesky orthonormalisation of W and P, stencil SpMV, Gram matrices,
+Rayleigh-Ritz, Ritz update) over the whole block.  Default workload: the 7-point Dirichlet
+Laplacian on a 128^3 interior grid (2,097,152 unknowns), m = 16 eigenpairs, 6-level V-cycle,
+float64 throughout.  The timed steps run with tol = 0 so that every column stays active (fixed
+work per step); the time to reach tol = 1e-8 is measured separately and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU) every rank solves an
+independent replica with its own seed ("replicas only": the solver has no data-path collective);
+`value` is the total iterations of all ranks / the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LOBPCG time-to-tol (s) & iters/s, 7-pt Laplacian, m eigenpairs; HBM % of peak"
+
+WORKLOADS = {
+    "c1": dict(dims=(48, 48, 48), m=8, levels=4),
+    "c2": dict(dims=(128, 128, 128), m=16, levels=6),
+    "c3": dict(dims=(256, 256, 256), m=32, levels=7),
+    "c4": dict(dims=(464, 464, 464), m=8, levels=8),
+}
+
+# FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM traffic per launch of the Gram kernel (steps 17-23) from one ncu capture, keyed by the
+# SHA-256 of the kernel source it was taken on; a changed source invalidates it (traffic = null).
+NCU_TRAFFIC = {}
+
+
+def workload_desc(w):
+    d = WORKLOADS[w]
+    n = d["dims"][0] * d["dims"][1] * d["dims"][2]
+    return (f"7-point Dirichlet Laplacian {d['dims'][0]}x{d['dims'][1]}x{d['dims'][2]} ({n:,} unknowns), "
+            f"m={d['m']}, {d['levels']}-level GMG V-cycle (2+2 weighted Jacobi, w=2/3), float64")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def gram_flops_per_launch(n, m):
+    """Algorithmic flops of steps 17-23 at b = m: upper triangles of gramA and gramB, q = 3m."""
+    q = 3 * m
+    return 2.0 * n * 2 * (q * (q + 1) // 2)
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", "k_block.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def cpu_baseline_sample(w, iters=1):
+    """The oracle (numpy/scipy float64) timed on this host for `iters` iterations of workload w."""
+    import numpy as np  # noqa: F401
+    from oracle import lobpcg as olob, multigrid, rng
+    d = WORKLOADS[w]
+    A = olob.Laplace7(d["dims"])
+    T = multigrid.VCycle(d["dims"], A.scale, d["levels"])
+    X0 = rng.uniform_block(2, A.n, d["m"])
+    marks = []
+    # iters + 1 passes; the spacing of the pass ends excludes the setup steps 1-5 and pass 0
+    # (pass 0 has no P block)
+    olob.lobpcg(A, X0, 0.0, iters + 1, T=T, on_pass=lambda k: marks.append(time.perf_counter()))
+    per = (marks[-1] - marks[0]) / (len(marks) - 1)
+    return 1.0 / per, per
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = args.workload
+    d = WORKLOADS[w]
+    steps = max(1, min(args.steps, 2))
+    warm = 1
+    ips, per = cpu_baseline_sample(w, iters=steps)
+    cores = os.cpu_count()
+    line = dict(impl="reference", metric=METRIC, value=ips, unit="iters/s", n_gpus=args.gpus, steps=steps,
+                warmup=warm, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=workload_desc(w), grid=list(d["dims"]), m=d["m"], levels=d["levels"]),
+                cpu_baseline=dict(value=ips, unit="iters/s", cores=cores, kind="oracle",
+                                  sample=f"{steps} oracle LOBPCG iteration(s) of the same workload after its setup and pass 0 "
+                                         "(numpy elementwise ops single-threaded, BLAS calls multi-threaded)"),
+                e2e=dict(value=ips, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_0705_2626_gb300.solver import Solver
+
+    w = args.workload
+    d = WORKLOADS[w]
+    dims, m, levels = d["dims"], d["m"], d["levels"]
+    n = dims[0] * dims[1] * dims[2]
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    seed = 2 + rank
+    s = Solver(dims, levels=levels, device=local_rank)
+    stream = s.stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- main timed region: K iterations with every column active, inputs resident in HBM
+    s.begin(m, tol=0.0, seed=seed)
+    s.iterate(args.warmup)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.iterate(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    launches = s.info.kernel_launches
+    t_ms = e0.elapsed_time(e1)
+    tt = torch.tensor([t_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_ms = float(tt.item())
+    value = world * args.steps / (t_ms / 1e3)
+
+    # ---- per-phase device times (events inside the library, same stream) for the roofline
+    s.set_options(phase_timing=True)
+    s.begin(m, tol=0.0, seed=seed)
+    s.iterate(args.warmup)
+    before = list(s.info.phase_ms)
+    s.iterate(args.steps)
+    after = list(s.info.phase_ms)
+    phase = {nm: (after[i] - before[i]) / args.steps for i, nm in enumerate(
+        ["residual", "precond", "cholqr_w", "spmv", "cholqr_p", "gram", "rayleigh_ritz", "update"])}
+    s.set_options(phase_timing=False)
+    gram_ms = phase["gram"]
+    gflop = gram_flops_per_launch(n, m)
+    achieved = gflop / (gram_ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get((w, kernel_source_hash()))
+
+    # ---- time to tolerance (tol 1e-8), device time of the iteration loop
+    out = s.solve(m, tol=1e-8, maxit=200, seed=seed)
+    ttt = dict(time_to_tol_s=(out["solve_ms"]) / 1e3, setup_s=out["setup_ms"] / 1e3, iters=out["iters"],
+               status=out["status_name"], max_rel_resid=out["max_rel_resid"], tol=1e-8)
+
+    # ---- end to end through the public API with host buffers: X0 from pinned host memory in,
+    # eigenvalues and eigenvectors back to pinned host memory, K iterations (tol 0)
+    X0 = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    X0.uniform_(-1.0, 1.0, generator=torch.Generator().manual_seed(seed))
+    Xout = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.set_initial(X0)
+    s.solve(m, tol=0.0, maxit=args.steps, seed=seed)
+    import ctypes
+    from paper_0705_2626_gb300 import capi
+    lam = (ctypes.c_double * m)()
+    capi.lobpcg_get_eigenpairs(s.h, lam, ctypes.c_void_p(Xout.data_ptr()), n, 1, None)
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = dict(value=world * args.steps / float(te.item()), unit="iters/s",
+               h2d_bytes_per_step=n * m * 8 / args.steps, d2h_bytes_per_step=(n * m * 8 + m * 8) / args.steps,
+               note="set_initial(host X0) + solve(tol=0, maxit=K) + get_eigenpairs(host), wall clock")
+    s.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ips, per = cpu_baseline_sample(w, iters=1)
+        cpu = dict(value=ips, unit="iters/s", cores=os.cpu_count(), kind="oracle",
+                   sample="1 oracle LOBPCG iteration of the same workload after its setup and pass 0 "
+                          "(numpy elementwise single-threaded, BLAS multi-threaded)")
+    line = dict(
+        metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic",
+        config=dict(workload=workload_desc(w), grid=list(dims), m=m, levels=levels, tol_timed=0.0,
+                    l2="no flush: the 6 stored blocks are 1.6 GB, far above the 129 MB L2",
+                    parallelism="replicas" if world > 1 else "single-gpu"),
+        time_to_tol=ttt, phase_ms_per_iter=phase,
+        roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles)", bound="alu",
+                      achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=achieved / FP64_PEAK_TFLOPS,
+                      traffic=traffic, peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
+        cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -96,6 +96,7 @@ typedef struct lobpcg_info {
     double  max_rel_resid;   /* max_j ||A x_j - l_j x_j|| / |l_j|, from A X at exit */
     double  setup_ms;        /* device time of steps 1-5                           */
     double  solve_ms;        /* device time of the iteration loop                  */
+    int64_t kernel_launches; /* kernels this library launched during the call       */
     double  phase_ms[LOBPCG_NPHASES];  /* device time per phase, summed over iterations;
                                           filled only when phase timing is enabled */
 } lobpcg_info;

@@ -61,8 +61,11 @@ def _converged(norm, lam, tol, tol_mode):
     return norm <= bound
 
 
-def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False):
-    """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity)."""
+def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False, on_pass=None):
+    """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity).
+
+    ``on_pass(k)`` (optional) is called after steps 9-33 of pass k, for timing only.
+    """
     X = np.array(X0, dtype=np.float64, copy=True)
     n, m = X.shape
     hist = []
@@ -167,6 +170,8 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
             AP = AP + APJ @ CP
         X = X @ CX + P
         AX = AX @ CX + AP
+        if on_pass is not None:
+            on_pass(k)
 
     resid = np.linalg.norm(A(X) - X * lam[None, :], axis=0)
     return Result(lam, X, iters, status, resid, hist)

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -12,6 +13,8 @@
 #include "../../include/lobpcg_gb300.h"
 
 namespace lg {
+
+extern std::atomic<long long> g_kernel_launches;
 
 struct Error : std::runtime_error {
     int code;
@@ -25,7 +28,12 @@ struct Error : std::runtime_error {
             throw ::lg::Error(LOBPCG_ERR_CUDA, std::string(#call) + ": " +             \
                                                    cudaGetErrorString(e_));            \
     } while (0)
-#define LG_CHECK_LAUNCH() LG_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by LG_CHECK_LAUNCH, which also counts it.
+#define LG_CHECK_LAUNCH()                                                              \
+    do {                                                                               \
+        ::lg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);               \
+        LG_CUDA(cudaGetLastError());                                                   \
+    } while (0)
 #define LG_REQUIRE(cond, code, msg)                                                    \
     do {                                                                               \
         if (!(cond)) throw ::lg::Error((code), (msg));                                 \

@@ -18,6 +18,10 @@
 
 using namespace lg;
 
+namespace lg {
+std::atomic<long long> g_kernel_launches{0};
+}
+
 namespace {
 
 struct DBuf {
@@ -82,6 +86,7 @@ struct lobpcg_handle {
     double phase_ms[LOBPCG_NPHASES] = {};
     cudaEvent_t ev[LOBPCG_NPHASES + 2] = {};
     int last_status = LOBPCG_OK;
+    long long launches_at_start = 0;
 };
 
 namespace {
@@ -509,6 +514,7 @@ void fill_info(lobpcg_t* h, lobpcg_info* out, int status) {
         mr = std::max(mr, h->resid_h[j] / std::fabs(h->lam_h[j]));
     out->max_rel_resid = mr;
     out->setup_ms = h->setup_ms;
+    out->kernel_launches = g_kernel_launches.load() - h->launches_at_start;
     out->solve_ms = h->solve_ms;
     for (int i = 0; i < LOBPCG_NPHASES; ++i) out->phase_ms[i] = h->phase_ms[i];
 }
@@ -694,6 +700,7 @@ int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on
 }
 
 int lobpcg_begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
+    if (h) h->launches_at_start = g_kernel_launches.load();
     return guarded(h, [&] {
         h->state = 0;
         begin(h, m, tol, seed);
@@ -702,6 +709,7 @@ int lobpcg_begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
 }
 
 int lobpcg_iterate(lobpcg_t* h, int steps, lobpcg_info* out) {
+    if (h) h->launches_at_start = g_kernel_launches.load();
     int rc = guarded(h, [&] {
         LG_REQUIRE(h->state == 1, LOBPCG_ERR_STATE, "call lobpcg_begin first");
         LG_REQUIRE(steps >= 0, LOBPCG_ERR_ARG, "steps must be >= 0");
@@ -725,6 +733,7 @@ int lobpcg_finish(lobpcg_t* h, lobpcg_info* out) {
 }
 
 int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed, lobpcg_info* out) {
+    if (h) h->launches_at_start = g_kernel_launches.load();
     int rc = guarded(h, [&] {
         LG_REQUIRE(maxit >= 0, LOBPCG_ERR_ARG, "maxit must be >= 0");
         h->state = 0;

@@ -130,6 +130,11 @@ class Solver:
         _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
         return rc
 
+    def set_options(self, tol_mode="relative", gram="explicit", phase_timing=False):
+        _check(capi.lobpcg_set_options(self.h, capi.TOL_RELATIVE if tol_mode == "relative" else capi.TOL_ABSOLUTE,
+                                       capi.GRAM_EXPLICIT if gram == "explicit" else capi.GRAM_PAPER,
+                                       1 if phase_timing else 0), self.h)
+
     def finish(self):
         rc = capi.lobpcg_finish(self.h, ctypes.byref(self.info))
         _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
@@ -149,5 +154,5 @@ class Solver:
         return dict(lam=list(lam), resid=list(res), X=X, iters=self.info.iters, status=self.info.status,
                     status_name=capi.STATUS_NAMES.get(self.info.status), active=self.info.active,
                     p_dropped=self.info.p_dropped, setup_ms=self.info.setup_ms, solve_ms=self.info.solve_ms,
-                    max_rel_resid=self.info.max_rel_resid,
+                    max_rel_resid=self.info.max_rel_resid, kernel_launches=self.info.kernel_launches,
                     phase_ms=dict(zip(capi.PHASE_NAMES, list(self.info.phase_ms))))
