@@ -167,7 +167,8 @@ int lobpcg_get_eigenpairs(lobpcg_t* h, double* lambda, double* X, int64_t ldx,
                           int x_on_host, double* resid);
 
 /* Text of the last error on this handle ("" if none).  Valid until the next
- * call on the handle.  h may be NULL (returns the last lobpcg_create error). */
+ * call on the handle.  h may be NULL: then the last error of a handle-free call
+ * (lobpcg_create, lobpcg_gram_noalloc) on the calling thread. */
 const char* lobpcg_last_error(const lobpcg_t* h);
 
 /* Release the handle and all of its workspace.  NULL is accepted. */
@@ -222,6 +223,32 @@ int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld);
  * ERR_BREAKDOWN if gramB is not numerically positive definite. */
 int lobpcg_op_rayleigh_ritz(lobpcg_t* h, int q, int m, const double* gramA,
                             const double* gramB, double* lambda, double* C);
+
+/* ---- allocation-free entry point -----------------------------------------
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory -- code running inside a host callback or signal
+ * handler, an application whose memory pool owns every byte of the device and
+ * forbids libraries to allocate, a latency-critical loop where an allocation
+ * could stall, or any caller without a handle (a handle allocates workspace).
+ *
+ * lobpcg_gram_noalloc computes exactly what lobpcg_op_gram computes (gramA =
+ * (S^T AS + AS^T S)/2 and gramB = S^T S for S = [S0 S1 S2], widths w0, w1, w2,
+ * n rows, common leading dimension ld; AS0 = NULL skips gramA) without a handle
+ * and without allocating: its per-block partial sums go to one fixed array of
+ * 8 MiB of device memory that each GPU loading this library holds until the
+ * process exits.  All pointers are device pointers; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call returns
+ * without waiting for it.  Limit: q = w0 + w1 + w2 <= 96, else LOBPCG_ERR_ARG.
+ * No cudaMalloc, cudaFree or other allocating routine is called.  The first
+ * call on a device looks up the array's device address and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array: calls
+ * whose kernels may overlap on the GPU (unordered streams or threads) race and
+ * give wrong results, so order them.  Errors: LOBPCG_ERR_ARG, LOBPCG_ERR_CUDA;
+ * the message is returned by lobpcg_last_error(NULL) on the calling thread. */
+int lobpcg_gram_noalloc(const double* S0, const double* S1, const double* S2,
+                        const double* AS0, const double* AS1, const double* AS2,
+                        int64_t n, int64_t ld, int w0, int w1, int w2,
+                        double* gramA, double* gramB, void* stream);
 
 #ifdef __cplusplus
 }

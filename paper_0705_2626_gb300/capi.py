@@ -63,6 +63,8 @@ _SIGNATURES = {
                                c_int64, c_int, c_int, c_int, c_void_p, c_void_p]),
     "lobpcg_op_cholqr": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int64]),
     "lobpcg_op_rayleigh_ritz": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lobpcg_gram_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                    c_int64, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -169,3 +171,7 @@ def lobpcg_op_cholqr(h, b, V, AV, ld):
 
 def lobpcg_op_rayleigh_ritz(h, q, m, gramA, gramB, lam, C):
     return _call("lobpcg_op_rayleigh_ritz", h, q, m, gramA, gramB, lam, C)
+
+
+def lobpcg_gram_noalloc(S0, S1, S2, AS0, AS1, AS2, n, ld, w0, w1, w2, gramA, gramB, stream):
+    return _call("lobpcg_gram_noalloc", S0, S1, S2, AS0, AS1, AS2, n, ld, w0, w1, w2, gramA, gramB, stream)

@@ -29,9 +29,11 @@ struct DBuf {
     size_t bytes = 0;
 };
 
-thread_local std::string g_create_error;
-
 }  // namespace
+
+namespace lg {
+thread_local std::string g_handle_free_error;
+}
 
 struct lobpcg_handle {
     int device = 0;
@@ -571,17 +573,17 @@ int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocat
     if (!out) return LOBPCG_ERR_ARG;
     *out = nullptr;
     if (precision != LOBPCG_FP64) {
-        g_create_error = "only LOBPCG_FP64 is available";
+        g_handle_free_error = "only LOBPCG_FP64 is available";
         return LOBPCG_ERR_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
-        g_create_error = "invalid CUDA device";
+        g_handle_free_error = "invalid CUDA device";
         return device < 0 ? LOBPCG_ERR_ARG : LOBPCG_ERR_CUDA;
     }
     if (alloc && (!alloc->alloc || !alloc->free)) {
-        g_create_error = "allocator needs both alloc and free";
+        g_handle_free_error = "allocator needs both alloc and free";
         return LOBPCG_ERR_ARG;
     }
     lobpcg_t* h = new (std::nothrow) lobpcg_t();
@@ -596,10 +598,10 @@ int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocat
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         delete h;
-        g_create_error = "cudaSetDevice failed";
+        g_handle_free_error = "cudaSetDevice failed";
         return LOBPCG_ERR_CUDA;
     }
-    g_create_error.clear();
+    g_handle_free_error.clear();
     *out = h;
     return LOBPCG_OK;
 }
@@ -775,7 +777,7 @@ int lobpcg_get_eigenpairs(lobpcg_t* h, double* lambda, double* X, int64_t ldx, i
 }
 
 const char* lobpcg_last_error(const lobpcg_t* h) {
-    if (!h) return g_create_error.c_str();
+    if (!h) return g_handle_free_error.c_str();
     return h->err.c_str();
 }
 
