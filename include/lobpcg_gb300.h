@@ -202,8 +202,10 @@ int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X,
 
 /* Gram matrices (Algorithm steps 17-23): S = [S0 S1 S2] with widths w0, w1, w2
  * (w1, w2 may be 0), each block n rows with leading dimension ld; AS likewise.
- * Writes the q-by-q (q = w0 + w1 + w2) column-major device matrices
- * gramA = (S^T AS + AS^T S)/2 and gramB = S^T S.  AS0 may be NULL (gramA skipped).
+ * Writes the q-by-q (q = w0 + w1 + w2) column-major device matrices gramB = S^T S
+ * and gramA with the block structure printed in steps 18 / 21: block (I, J) =
+ * S_I^T AS_J for I < J, its transpose below the diagonal, and (S_I^T AS_I +
+ * AS_I^T S_I)/2 on the diagonal.  AS0 may be NULL (gramA skipped).
  * Deterministic: partial sums per thread block are added in a fixed order. */
 int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double* S2,
                    const double* AS0, const double* AS1, const double* AS2,
@@ -231,9 +233,9 @@ int lobpcg_op_rayleigh_ritz(lobpcg_t* h, int q, int m, const double* gramA,
  * forbids libraries to allocate, a latency-critical loop where an allocation
  * could stall, or any caller without a handle (a handle allocates workspace).
  *
- * lobpcg_gram_noalloc computes exactly what lobpcg_op_gram computes (gramA =
- * (S^T AS + AS^T S)/2 and gramB = S^T S for S = [S0 S1 S2], widths w0, w1, w2,
- * n rows, common leading dimension ld; AS0 = NULL skips gramA) without a handle
+ * lobpcg_gram_noalloc computes what lobpcg_op_gram computes (gramA and gramB of
+ * S = [S0 S1 S2], widths w0, w1, w2, n rows, common leading dimension ld; AS0 =
+ * NULL skips gramA) without a handle
  * and without allocating: its per-block partial sums go to one fixed array of
  * 8 MiB of device memory that each GPU loading this library holds until the
  * process exits.  All pointers are device pointers; the work is enqueued on

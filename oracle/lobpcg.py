@@ -15,9 +15,11 @@ Readings of points the paper leaves open (each listed in the design notes):
   (``"absolute"``, the paper's literal wording); J only shrinks.
 * loop bound (step 6, k = 0..MaxIterations): the pass k = maxit performs only
   steps 7-8; ``iters`` is the k at which J became empty.
-* Gram blocks (steps 18-22): computed explicitly, including the diagonal blocks
-  the paper sets to Lambda and I, and symmetrised (G + G^T)/2 (the MATLAB
-  variant the paper reports as more accurate).  ``gram="paper"`` sets them as
+* Gram blocks (steps 18-22): the paper prints only the upper block triangle of
+  gramA (the blocks below the diagonal are its transposes); those blocks are
+  computed, including the diagonal blocks the paper sets to Lambda and I, which
+  are symmetrised (G + G^T)/2 (the explicit variant the paper reports as more
+  accurate).  gramB = S^T S.  ``gram="paper"`` sets the diagonal blocks as
   printed in the algorithm.
 * Cholesky (steps 3, 11, 14): scale-invariant via unit-diagonal scaling.
 * breakdown: if chol(P_J^T P_J) or the Rayleigh-Ritz with P fails, the P block
@@ -54,6 +56,23 @@ class Laplace7:
 
     def __call__(self, U):
         return laplace.apply(U, self.dims, self.scale)
+
+
+def upper_block_gram(S, AS):
+    """gramA of steps 18 / 21: blocks S_I^T AS_J for I <= J, lower blocks by symmetry,
+    diagonal blocks symmetrised."""
+    widths = [b.shape[1] for b in S]
+    offs = np.concatenate([[0], np.cumsum(widths)])
+    q = int(offs[-1])
+    G = np.empty((q, q))
+    for I in range(len(S)):
+        for J in range(I, len(S)):
+            blk = S[I].T @ AS[J]
+            if I == J:
+                blk = symmetrize(blk)
+            G[offs[I]:offs[I + 1], offs[J]:offs[J + 1]] = blk
+            G[offs[J]:offs[J + 1], offs[I]:offs[I + 1]] = blk.T
+    return G
 
 
 def _converged(norm, lam, tol, tol_mode):
@@ -134,8 +153,8 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
         while True:
             S = [X, W] + ([PJ] if use_p else [])
             AS = [AX, AW] + ([APJ] if use_p else [])
-            Sm, ASm = np.hstack(S), np.hstack(AS)
-            gramA = symmetrize(Sm.T @ ASm)
+            Sm = np.hstack(S)
+            gramA = upper_block_gram(S, AS)
             gramB = symmetrize(Sm.T @ Sm)
             if gram == "paper":
                 gramA[:m, :m] = np.diag(lam)

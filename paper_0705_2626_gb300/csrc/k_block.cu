@@ -88,7 +88,6 @@ __global__ void k_norms_finalize(int nchunks, const double* __restrict__ partial
 }
 
 // ------------------------------------------------------------------ Gram
-constexpr int kGK = 16;   // grid points per shared-memory stage
 constexpr int kTM = 4;    // each thread owns a kTM x kTM tile of the output
 
 __device__ __forceinline__ const double* col_ptr(const Blocks3& B, int c) {
@@ -99,31 +98,68 @@ __device__ __forceinline__ const double* col_ptr(const Blocks3& B, int c) {
     return B.p[2] + (int64_t)c * B.ld;
 }
 
-// Partial sums of S^T AS (all q x q entries, "A") and S^T S (upper tiles, "B") over one row
-// range per thread block.  Output tile (ti, tj) of the A part uses S columns of row tile ti and
-// AS columns of column tile tj; tiles are numbered row-major so that the threads of a warp
-// share ti (broadcast shared-memory reads of S) and walk along tj.
+__host__ __device__ inline int block_of(const Blocks3& B, int c) {
+    return c < B.w[0] ? 0 : (c < B.w[0] + B.w[1] ? 1 : 2);
+}
+
+// Output tile (ti, tj) of S^T AS is needed when it holds an entry (i, j) with
+// block(i) <= block(j): the upper block triangle of steps 18 / 21, diagonal blocks in full.
+__host__ __device__ inline bool a_tile_needed(const Blocks3& B, int q, int ti, int tj) {
+    return block_of(B, ti * kTM) <= block_of(B, min(tj * kTM + kTM - 1, q - 1));
+}
+
+struct GramShape {
+    int ntA, ntB, ks, gk;    // needed A tiles, upper B tiles, row groups, rows per stage
+};
+
+__host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a) {
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    GramShape g;
+    g.ntA = 0;
+    if (with_a)
+        for (int ti = 0; ti < T; ++ti)
+            for (int tj = 0; tj < T; ++tj) g.ntA += a_tile_needed(S, q, ti, tj);
+    g.ntB = T * (T + 1) / 2;
+    const int nt = g.ntA + g.ntB;
+    g.ks = max(1, min(8, 256 / nt));     // narrow bases: several row groups per tile
+    // keep the stage buffers and the group reduction within 48 KB of shared memory
+    while (g.ks > 1 && max(2 * 16 * g.ks * (T * kTM + 1), g.ks * nt * 16) * 8 > 48 * 1024) --g.ks;
+    g.gk = 16 * g.ks;
+    return g;
+}
+
+// Partial sums over one row range per thread block of the needed tiles of S^T AS ("A") and of
+// the upper tiles of S^T S ("B").  Thread t works on tile t % nt for the rows of each
+// shared-memory stage congruent to t / nt modulo ks; the ks row groups are added in a fixed
+// order at the end.  Tiles are numbered row-major, so a warp shares ti (broadcast reads of S).
 __global__ void __launch_bounds__(1024)
     k_gram(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
-                       double* __restrict__ part) {
+           double* __restrict__ part) {
     extern __shared__ double sm[];
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
+    const GramShape gs = gram_shape(S, with_a != 0);
+    const int nt = gs.ntA + gs.ntB;
     const int ldsm = T * kTM + 1;                 // odd row length: conflict-free stores
-    double* sS = sm;                              // [kGK][ldsm]
-    double* sA = sm + kGK * ldsm;                 // [kGK][ldsm]
-    const int ntA = with_a ? T * T : 0;
-    const int ntB = T * (T + 1) / 2;
-    const int tile = threadIdx.x;
-    const bool active = tile < ntA + ntB;
-    const bool isA = tile < ntA;
+    double* sS = sm;                              // [gk][ldsm]
+    double* sA = sm + gs.gk * ldsm;               // [gk][ldsm]
+    const int tile = threadIdx.x % nt;
+    const int grp = threadIdx.x / nt;
+    const bool active = grp < gs.ks;
+    const bool isA = tile < gs.ntA;
     int ti = 0, tj = 0;
     if (isA) {
-        ti = tile / T;
-        tj = tile - ti * T;
-    } else if (active) {
-        int u = tile - ntA;                       // upper tiles ti <= tj, row-major
-        ti = 0;
+        int u = tile;                             // u-th needed A tile, row-major
+        for (int a = 0; a < T * T; ++a) {
+            const int ai = a / T, aj = a % T;
+            if (a_tile_needed(S, q, ai, aj)) {
+                if (u == 0) { ti = ai; tj = aj; break; }
+                --u;
+            }
+        }
+    } else {
+        int u = tile - gs.ntA;                    // upper B tiles ti <= tj, row-major
         while (u >= T - ti) { u -= T - ti; ++ti; }
         tj = ti + u;
     }
@@ -136,9 +172,9 @@ __global__ void __launch_bounds__(1024)
     const int64_t r0 = blockIdx.x * rows_per_part;
     const int64_t r1 = min(n, r0 + rows_per_part);
     const double* rhs = isA ? sA : sS;
-    for (int64_t base = r0; base < r1; base += kGK) {
-        for (int e = threadIdx.x; e < kGK * T * kTM; e += blockDim.x) {
-            const int c = e / kGK, k = e - c * kGK;
+    for (int64_t base = r0; base < r1; base += gs.gk) {
+        for (int e = threadIdx.x; e < gs.gk * T * kTM; e += blockDim.x) {
+            const int c = e / gs.gk, k = e - c * gs.gk;
             const int64_t p = base + k;
             double vs = 0.0, va = 0.0;
             if (c < q && p < r1) {
@@ -151,7 +187,7 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
         if (active) {
 #pragma unroll 4
-            for (int k = 0; k < kGK; ++k) {
+            for (int k = grp; k < gs.gk; k += gs.ks) {
                 double a[kTM], b[kTM];
 #pragma unroll
                 for (int u = 0; u < kTM; ++u) {
@@ -166,7 +202,27 @@ __global__ void __launch_bounds__(1024)
         }
         __syncthreads();
     }
-    if (!active) return;
+    // add the row groups in order 0, 1, ..., ks-1 (the stage buffers are free now)
+    if (gs.ks > 1) {
+        double* red = sm;                          // [ks][nt][16]
+        if (active)
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = acc[u][v];
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) {
+                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
+                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
+                    acc[u][v] = sum;
+                }
+        }
+    }
+    if (grp != 0) return;
     double* out = part + (int64_t)blockIdx.x * 2 * q * q + (isA ? 0 : (int64_t)q * q);
 #pragma unroll
     for (int u = 0; u < kTM; ++u)
@@ -177,10 +233,11 @@ __global__ void __launch_bounds__(1024)
         }
 }
 
-// One warp per unordered pair (i <= j): fixed-order sums of the partials.
+// One warp per unordered pair (i <= j): fixed-order sums of the partials.  gramA(i, j) is the
+// symmetrised sum inside a diagonal block and the upper-block entry S_i^T AS_j otherwise.
 __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ part, int with_a,
                                 double* __restrict__ gA, double* __restrict__ gB,
-                                const double* __restrict__ paper_lam, int w0, int w1, int w2) {
+                                const double* __restrict__ paper_lam, Blocks3 W) {
     const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t npairs = (int64_t)q * (q + 1) / 2;
@@ -189,6 +246,7 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
     int64_t u = pair;
     while (u >= j + 1) { u -= j + 1; ++j; }       // column j, row i <= j
     const int i = (int)u;
+    const bool same = block_of(W, i) == block_of(W, j);
     const int64_t q2 = (int64_t)q * q;
     double sb = 0.0, sa1 = 0.0, sa2 = 0.0;
     for (int c = lane; c < nparts; c += 32) {
@@ -196,19 +254,18 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
         sb += P[q2 + i + (int64_t)q * j];
         if (with_a) {
             sa1 += P[i + (int64_t)q * j];
-            sa2 += P[j + (int64_t)q * i];
+            if (same) sa2 += P[j + (int64_t)q * i];
         }
     }
     sb = warp_sum(sb);
     sa1 = warp_sum(sa1);
     sa2 = warp_sum(sa2);
     if (lane) return;
-    double a = 0.5 * (sa1 + sa2);
+    double a = same ? 0.5 * (sa1 + sa2) : sa1;
     double b = sb;
     if (paper_lam) {
-        auto blk = [&](int c) { return c < w0 ? 0 : (c < w0 + w1 ? 1 : 2); };
-        if (i < w0 && j < w0) a = (i == j) ? paper_lam[i] : 0.0;
-        if (blk(i) == blk(j)) b = (i == j) ? 1.0 : 0.0;
+        if (block_of(W, i) == 0 && block_of(W, j) == 0) a = (i == j) ? paper_lam[i] : 0.0;
+        if (same) b = (i == j) ? 1.0 : 0.0;
     }
     if (with_a) { gA[i + (int64_t)q * j] = a; gA[j + (int64_t)q * i] = a; }
     gB[i + (int64_t)q * j] = b;
@@ -331,7 +388,7 @@ void launch_norms_finalize(int ncols, int nchunks, const double* partial, double
 }
 
 int gram_parts(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 64 * kGK), 2 * kNumSMs));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 1024), 2 * kNumSMs));
 }
 
 int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n) * 2 * q * q; }
@@ -340,10 +397,14 @@ void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, i
                  cudaStream_t st) {
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
-    const int ntiles = (AS ? T * T : 0) + T * (T + 1) / 2;
-    const int threads = (int)std::max<int64_t>(64, ceil_div(ntiles, 32) * 32);
+    const GramShape gs = gram_shape(S, AS != nullptr);
+    const int nt = gs.ntA + gs.ntB;
+    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
     LG_REQUIRE(threads <= 1024, LOBPCG_ERR_ARG, "Gram basis too wide");
-    const size_t smem = 2 * kGK * (size_t)(T * kTM + 1) * sizeof(double);
+    const size_t stage = 2 * (size_t)gs.gk * (T * kTM + 1);
+    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 : 0;
+    const size_t smem = std::max(stage, red) * sizeof(double);
+    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
     const int64_t rows = ceil_div(n, nparts);
     Blocks3 A = AS ? *AS : S;
     k_gram<<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
@@ -355,10 +416,11 @@ void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, do
                           cudaStream_t st) {
     const int64_t npairs = (int64_t)q * (q + 1) / 2;
     const int64_t threads = npairs * 32;
-    const int w0 = widths ? widths->w[0] : q, w1 = widths ? widths->w[1] : 0,
-              w2 = widths ? widths->w[2] : 0;
+    Blocks3 W{};
+    if (widths) W = *widths;
+    else { W.w[0] = q; W.w[1] = 0; W.w[2] = 0; }
     k_gram_finalize<<<(unsigned)ceil_div(threads, 256), 256, 0, st>>>(
-        q, nparts, part, with_a ? 1 : 0, gramA, gramB, paper_lambda, w0, w1, w2);
+        q, nparts, part, with_a ? 1 : 0, gramA, gramB, paper_lambda, W);
     LG_CHECK_LAUNCH();
 }
 

@@ -12,7 +12,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import dense, laplace, multigrid, rng  # noqa: E402
+from oracle import dense, laplace, lobpcg as olob, multigrid, rng  # noqa: E402
 from paper_0705_2626_gb300 import capi  # noqa: E402
 from paper_0705_2626_gb300.solver import Solver  # noqa: E402
 from tests.gpu_util import dev, empty, host, ptr  # noqa: E402
@@ -120,7 +120,10 @@ def test_gram_matches_definition(dims, widths):
     assert rc == capi.OK
     # device matrices are column-major: element (i, j) at i + q*j -> transpose of the row-major view
     GA, GB = gA.cpu().numpy().T, gB.cpu().numpy().T
-    wantA = dense.symmetrize(S.T @ AS)
+    offs = np.concatenate([[0], np.cumsum(widths)])
+    Sb = [S[:, offs[i]:offs[i + 1]] for i in range(3) if widths[i]]
+    ASb = [AS[:, offs[i]:offs[i + 1]] for i in range(3) if widths[i]]
+    wantA = olob.upper_block_gram(Sb, ASb)      # steps 18 / 21: upper block triangle
     wantB = S.T @ S
     nrmS, nrmA = np.linalg.norm(S, axis=0), np.linalg.norm(AS, axis=0)
     boundA = 2 * n * EPS * (np.outer(nrmS, nrmA) + np.outer(nrmA, nrmS)) / 2
