@@ -50,7 +50,9 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------ */
 #define LOBPCG_FP64            0   /* every step in float64                 */
-#define LOBPCG_MIXED           1   /* reserved for the mixed-precision form */
+#define LOBPCG_MIXED           1   /* X, AX, small matrices float64; W / P family float32;
+                                      V-cycle float32 with bfloat16 coarse levels; Gram in
+                                      float32 with compensated sums; float64 final check */
 
 #define LOBPCG_LAPLACE7        0   /* constant-coefficient 7-point stencil  */
 
@@ -93,6 +95,8 @@ typedef struct lobpcg_info {
     int32_t iters;           /* iterations performed (k at which J became empty)  */
     int32_t active;          /* |J| at exit                                       */
     int32_t p_dropped;       /* iterations in which the P block was dropped       */
+    int32_t fp64_sweeps;     /* mixed form: float64 correction sweeps performed   */
+    int32_t reserved;
     double  max_rel_resid;   /* max_j ||A x_j - l_j x_j|| / |l_j|, from A X at exit */
     double  setup_ms;        /* device time of steps 1-5                           */
     double  solve_ms;        /* device time of the iteration loop                  */
@@ -104,7 +108,11 @@ typedef struct lobpcg_info {
 /* ---- solver-level entry points ------------------------------------------ */
 
 /* Create a handle on CUDA device `device`.  `stream` is a cudaStream_t (NULL =
- * the legacy default stream); `alloc` may be NULL; `precision` is LOBPCG_FP64.
+ * the legacy default stream); `alloc` may be NULL; `precision` is LOBPCG_FP64
+ * or LOBPCG_MIXED.  In the mixed form, once every implicit residual passes the
+ * tolerance, a float64 correction sweep (steps 3-4 of the algorithm on the
+ * current X with a float64 A X) recomputes the Ritz pairs and their residuals;
+ * columns that still fail re-enter the iteration (at most 8 sweeps).
  * On success *h receives the handle.  Errors: ERR_ARG, ERR_CUDA. */
 int lobpcg_create(lobpcg_t** h, int device, void* stream,
                   const lobpcg_allocator* alloc, int precision);
@@ -189,7 +197,7 @@ int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx,
                       double* Y, int64_t ldy);
 
 /* E = T R for `ncols` columns (Algorithm step 9; T = I copies): device R, E,
- * which must not overlap. */
+ * which must not overlap.  Needs a LOBPCG_FP64 handle. */
 int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,
                       double* E, int64_t lde);
 

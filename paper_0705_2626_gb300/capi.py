@@ -37,7 +37,8 @@ class Allocator(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("active", ctypes.c_int32),
-                ("p_dropped", ctypes.c_int32), ("max_rel_resid", c_double), ("setup_ms", c_double),
+                ("p_dropped", ctypes.c_int32), ("fp64_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_rel_resid", c_double), ("setup_ms", c_double),
                 ("solve_ms", c_double), ("kernel_launches", ctypes.c_int64), ("phase_ms", c_double * NPHASES)]
 
 

@@ -1,7 +1,7 @@
-// Shared definitions of the GB300 LOBPCG library: error type, grid geometry,
-// column lists and the host-side launchers of every kernel.  Kernels live in
-// k_stencil.cu (stencil family + V-cycle), k_block.cu (tall-skinny block ops)
-// and k_dense.cu (small dense factorizations on one thread block).
+// Shared definitions of the GB300 LOBPCG library: error type, grid geometry, storage types,
+// column lists and the host-side launchers of every kernel.  Kernels live in k_stencil.cu
+// (stencil family + V-cycle), k_block.cu (tall-skinny block ops) and k_dense.cu (small dense
+// factorizations on one thread block).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -66,67 +66,81 @@ enum StatusBits : unsigned {
     ST_NONFINITE = 16u,       // non-finite value in a small dense matrix
 };
 
+// Storage types of the blocks: float64 (FP64 form; X and AX of the mixed form), float32 (the
+// W / P family and level 0 of the V-cycle in the mixed form), bfloat16 (coarse V-cycle levels
+// of the mixed form).  Arithmetic is float64 on float64 data and float32 otherwise.
+enum DType : int { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+inline size_t dtype_size(DType t) { return t == DT_F64 ? 8 : (t == DT_F32 ? 4 : 2); }
+
 // ---------------------------------------------------------------- stencil family
-// y = a*x + b*(sum of the 6 neighbours of x) [+ c*z], per column, zero outside the grid.
-void launch_stencil_axpby(const Grid3& g, int ncols, double a, double b, const double* x,
-                          int64_t ldx, double c, const double* z, int64_t ldz, double* y,
+// y = a*x + b*(sum of the 6 neighbours of x) [+ c*z], per column, zero outside the grid;
+// x, z and y share the storage type t.
+void launch_stencil_axpby(const Grid3& g, int ncols, DType t, double a, double b, const void* x,
+                          int64_t ldx, double c, const void* z, int64_t ldz, void* y,
                           int64_t ldy, cudaStream_t st);
-// Full-weighting restriction rc = P^T rf / 8 (fine grid gf -> coarse grid gc).
-void launch_restrict(const Grid3& gf, const Grid3& gc, int ncols, const double* rf, int64_t ldf,
-                     double* rc, int64_t ldc, cudaStream_t st);
+// Full-weighting restriction rc = P^T rf / 8 (fine grid gf, type tf -> coarse grid gc, type tc).
+void launch_restrict(const Grid3& gf, const Grid3& gc, int ncols, DType tf, const void* rf,
+                     int64_t ldf, DType tc, void* rc, int64_t ldc, cudaStream_t st);
 // Trilinear prolongation with correction: ef += P ec.
-void launch_prolong_add(const Grid3& gf, const Grid3& gc, int ncols, const double* ec,
-                        int64_t ldc, double* ef, int64_t ldf, cudaStream_t st);
-// Exact coarsest-level solve e = A_c^-1 r through the discrete sine transform.
-// `tables` holds the three normalised 1-D sine matrices and the eigenvalues
-// (layout from coarse_tables_size / launch_coarse_setup).
+void launch_prolong_add(const Grid3& gf, const Grid3& gc, int ncols, DType tc, const void* ec,
+                        int64_t ldc, DType tf, void* ef, int64_t ldf, cudaStream_t st);
+// Exact coarsest-level solve e = A_c^-1 r through the discrete sine transform (float64
+// arithmetic for every storage type).  `tables` holds the three normalised 1-D sine matrices
+// and the eigenvalues (layout from coarse_tables_size / launch_coarse_setup).
 int64_t coarse_tables_size(const Grid3& g);
 void launch_coarse_setup(const Grid3& g, double scale, double* tables, cudaStream_t st);
-void launch_coarse_solve(const Grid3& g, int ncols, const double* tables, const double* r,
-                         int64_t ldr, double* e, int64_t lde, cudaStream_t st);
+void launch_coarse_solve(const Grid3& g, int ncols, DType t, const double* tables, const void* r,
+                         int64_t ldr, void* e, int64_t lde, cudaStream_t st);
+// Copy (with conversion) of ncols columns of n entries.
+void launch_convert(int64_t n, int ncols, DType ts, const void* src, int64_t lds, DType td,
+                    void* dst, int64_t ldd, cudaStream_t st);
 
 // ---------------------------------------------------------------- block ops
 void launch_random_block(uint64_t seed, int64_t n, int m, double* X, int64_t ldx,
                          cudaStream_t st);
-// Partial sums of squares of W[:, t] = AX[:, cols[t]] - lambda[cols[t]] * X[:, cols[t]];
-// writes W if non-null.  partial has nchunks * cols.n doubles.
+// Partial sums of squares of W[:, t] = AX[:, cols[t]] - lambda[cols[t]] * X[:, cols[t]]
+// (float64 arithmetic); writes W (type tw) if non-null.  partial has nchunks * cols.n doubles.
 int residual_chunks(int64_t n);
 void launch_residual(int64_t n, const ColList& cols, const double* X, const double* AX,
-                     int64_t ld, const double* lambda, double* W, int64_t ldw, double* partial,
-                     cudaStream_t st);
+                     int64_t ld, const double* lambda, DType tw, void* W, int64_t ldw,
+                     double* partial, cudaStream_t st);
 // norms[t] = sqrt(sum_c partial[t*nchunks + c]) in a fixed order.
 void launch_norms_finalize(int ncols, int nchunks, const double* partial, double* norms,
                            cudaStream_t st);
 
-// Block pointers of a basis [B0 B1 B2] (widths w[k], common leading dimension).
+// Block pointers of a basis [B0 B1 B2] (widths w[k], common leading dimension in elements).
+// Block 0 has storage type t0 (X or AX), blocks 1 and 2 type t12 (the W and P families).
 struct Blocks3 {
-    const double* p[3];
+    const void* p[3];
     int w[3];
     int64_t ld;
+    DType t0, t12;
     __host__ __device__ int q() const { return w[0] + w[1] + w[2]; }
 };
-// Gram partial sums over `nparts` row ranges: part has nparts * 2*q*q doubles.
+// Gram partial sums over `nparts` row ranges: part has nparts * 2*q*q doubles.  Float64
+// blocks only: float64 arithmetic; otherwise float32 products with compensated sums.
 int gram_parts(int64_t n);
 int64_t gram_scratch_doubles(int64_t n, int q);
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st);
-// gramA = (G + G^T)/2 of the summed A partials; gramB = summed B partials, mirrored.
-// If paper_lambda != null the X block of gramA is diag(lambda) and the diagonal blocks of
-// gramB are identities (steps 18-22 as printed).
+// gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
+// summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
+// diagonal blocks of gramB are identities (steps 18-22 as printed).
 void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, double* gramA,
                           double* gramB, const double* paper_lambda, const Blocks3* widths,
                           cudaStream_t st);
 
-// Vout = Vin Rinv for b columns (Rinv upper-triangular b x b, column-major, device).
-// Vout may equal Vin (in place).  Skipped if *status & skip_mask.
-void launch_apply_rinv(int64_t n, int b, const double* Vin, int64_t ldin, double* Vout,
+// Vout = Vin Rinv for b columns of type t (Rinv upper-triangular b x b, float64, column-major,
+// device).  Vout may equal Vin (in place).  Skipped if *status & skip_mask.
+void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void* Vout,
                        int64_t ldout, const double* Rinv, const unsigned* status,
                        unsigned skip_mask, cudaStream_t st);
-// Ritz update (steps 27-28 / 31-32): Pout = S1 C1 + S2 C2 and Xout = S0 C0 + Pout, with
-// C (q x m, column-major, ld q) split by rows into C0 (w0), C1 (w1), C2 (w2).
-// Xout may alias S0 and Pout may alias S2.  Skipped if *status & skip_mask.
+// Ritz update (steps 27-28 / 31-32): Pout = S1 C1 + S2 C2 (type of S1, S2) and
+// Xout = S0 C0 + Pout (float64), with C (q x m, column-major, ld q, float64) split by rows into
+// C0 (w0), C1 (w1), C2 (w2).  Xout may alias S0 and Pout may alias S2; Pout may be null.
+// Skipped if *status & skip_mask.
 void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout,
-                   double* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
+                   void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
                    cudaStream_t st);
 
 // ---------------------------------------------------------------- small dense

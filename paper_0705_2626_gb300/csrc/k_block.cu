@@ -5,10 +5,14 @@
 //   and the Cholesky Gram matrices of steps 3, 11, 14),
 //   multiplication by the inverse Cholesky factor (steps 3, 11, 14-15),
 //   the Ritz update of P, AP, X, AX (steps 25-33).
-// Reductions over the n grid points are deterministic: per-thread-block partial sums land
-// in scratch memory and are added in a fixed order by a second kernel, so repeated runs are
-// bit-identical.
+// Blocks are float64 in the FP64 form; in the mixed form X and AX stay float64 and the W / P
+// family is float32 (products in float32, sums compensated).  Reductions over the n grid points
+// are deterministic: per-thread-block partial sums land in scratch memory and are added in a
+// fixed order by a second kernel, so repeated runs are bit-identical.
+#include <type_traits>
+
 #include "common.cuh"
+#include "dtype.cuh"
 
 namespace lg {
 namespace {
@@ -55,10 +59,13 @@ __device__ double block_sum(double v, double* red) {
 
 constexpr int kResThreads = 256;
 
+// W[:, t] = AX[:, j] - lambda_j X[:, j] in float64 (stored as TW), j = cols[t]; the norms come
+// from the float64 values.
+template <typename TW>
 __global__ void __launch_bounds__(kResThreads)
     k_residual(int64_t n, int64_t rows_per_chunk, ColList cols, const double* __restrict__ X,
                const double* __restrict__ AX, int64_t ld, const double* __restrict__ lam,
-               double* __restrict__ W, int64_t ldw, double* __restrict__ partial, int nchunks) {
+               TW* __restrict__ W, int64_t ldw, double* __restrict__ partial, int nchunks) {
     __shared__ double red[32];
     const int t = blockIdx.y;
     const int j = cols.idx[t];
@@ -67,11 +74,11 @@ __global__ void __launch_bounds__(kResThreads)
     const int64_t r1 = min(n, r0 + rows_per_chunk);
     const double* xc = X + (int64_t)j * ld;
     const double* ac = AX + (int64_t)j * ld;
-    double* wc = W ? W + (int64_t)t * ldw : nullptr;
+    TW* wc = W ? W + (int64_t)t * ldw : nullptr;
     double acc = 0.0;
     for (int64_t p = r0 + threadIdx.x; p < r1; p += blockDim.x) {
         const double w = fma(-lj, __ldg(xc + p), __ldg(ac + p));
-        if (wc) wc[p] = w;
+        if (wc) st_as(wc + p, w);
         acc = fma(w, w, acc);
     }
     const double s = block_sum(acc, red);
@@ -90,12 +97,13 @@ __global__ void k_norms_finalize(int nchunks, const double* __restrict__ partial
 // ------------------------------------------------------------------ Gram
 constexpr int kTM = 4;    // each thread owns a kTM x kTM tile of the output
 
-__device__ __forceinline__ const double* col_ptr(const Blocks3& B, int c) {
-    if (c < B.w[0]) return B.p[0] + (int64_t)c * B.ld;
+template <typename T0, typename T12, typename C>
+__device__ __forceinline__ C load_col(const Blocks3& B, int c, int64_t p) {
+    if (c < B.w[0]) return (C)ld_as(static_cast<const T0*>(B.p[0]) + (int64_t)c * B.ld + p);
     c -= B.w[0];
-    if (c < B.w[1]) return B.p[1] + (int64_t)c * B.ld;
+    if (c < B.w[1]) return (C)ld_as(static_cast<const T12*>(B.p[1]) + (int64_t)c * B.ld + p);
     c -= B.w[1];
-    return B.p[2] + (int64_t)c * B.ld;
+    return (C)ld_as(static_cast<const T12*>(B.p[2]) + (int64_t)c * B.ld + p);
 }
 
 __host__ __device__ inline int block_of(const Blocks3& B, int c) {
@@ -112,7 +120,7 @@ struct GramShape {
     int ntA, ntB, ks, gk;    // needed A tiles, upper B tiles, row groups, rows per stage
 };
 
-__host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a) {
+__host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a, int elt) {
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
     GramShape g;
@@ -124,26 +132,33 @@ __host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a) {
     const int nt = g.ntA + g.ntB;
     g.ks = max(1, min(8, 256 / nt));     // narrow bases: several row groups per tile
     // keep the stage buffers and the group reduction within 48 KB of shared memory
-    while (g.ks > 1 && max(2 * 16 * g.ks * (T * kTM + 1), g.ks * nt * 16) * 8 > 48 * 1024) --g.ks;
+    while (g.ks > 1 && max(2 * 16 * g.ks * (T * kTM + 1) * elt, g.ks * nt * 16 * 8) > 48 * 1024) --g.ks;
     g.gk = 16 * g.ks;
     return g;
 }
 
 // Partial sums over one row range per thread block of the needed tiles of S^T AS ("A") and of
 // the upper tiles of S^T S ("B").  Thread t works on tile t % nt for the rows of each
-// shared-memory stage congruent to t / nt modulo ks; the ks row groups are added in a fixed
-// order at the end.  Tiles are numbered row-major, so a warp shares ti (broadcast reads of S).
-__global__ void __launch_bounds__(1024)
+// shared-memory stage congruent to t / nt modulo ks (16 rows per stage and thread); the ks
+// row groups are added in a fixed order at the end.  Tiles are numbered row-major, so a warp
+// shares ti (broadcast reads of S).  C = double: float64 products and sums.  C = float:
+// float32 products summed over the 16 rows of a stage, stage sums added with Kahan's
+// compensated summation, the result rounded to float64.
+constexpr int kGramMaxThreads = 768;   // q <= 96: at most 684 tiles of 4 x 4
+
+template <typename T0, typename T12, typename C>
+__global__ void __launch_bounds__(kGramMaxThreads)
     k_gram(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
            double* __restrict__ part) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sm = reinterpret_cast<C*>(sm_raw);
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
-    const GramShape gs = gram_shape(S, with_a != 0);
+    const GramShape gs = gram_shape(S, with_a != 0, (int)sizeof(C));
     const int nt = gs.ntA + gs.ntB;
     const int ldsm = T * kTM + 1;                 // odd row length: conflict-free stores
-    double* sS = sm;                              // [gk][ldsm]
-    double* sA = sm + gs.gk * ldsm;               // [gk][ldsm]
+    C* sS = sm;                                   // [gk][ldsm]
+    C* sA = sm + gs.gk * ldsm;                    // [gk][ldsm]
     const int tile = threadIdx.x % nt;
     const int grp = threadIdx.x / nt;
     const bool active = grp < gs.ks;
@@ -163,23 +178,25 @@ __global__ void __launch_bounds__(1024)
         while (u >= T - ti) { u -= T - ti; ++ti; }
         tj = ti + u;
     }
-    double acc[kTM][kTM];
+    C acc[kTM][kTM];          // running sums (float64), or the current stage's sums (float32)
+    C cmp[kTM][kTM];          // Kahan compensation (float32 only)
+    C tot[kTM][kTM];          // compensated running sums (float32 only)
 #pragma unroll
     for (int a = 0; a < kTM; ++a)
 #pragma unroll
-        for (int b = 0; b < kTM; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < kTM; ++b) acc[a][b] = cmp[a][b] = tot[a][b] = C(0);
 
     const int64_t r0 = blockIdx.x * rows_per_part;
     const int64_t r1 = min(n, r0 + rows_per_part);
-    const double* rhs = isA ? sA : sS;
+    const C* rhs = isA ? sA : sS;
     for (int64_t base = r0; base < r1; base += gs.gk) {
         for (int e = threadIdx.x; e < gs.gk * T * kTM; e += blockDim.x) {
             const int c = e / gs.gk, k = e - c * gs.gk;
             const int64_t p = base + k;
-            double vs = 0.0, va = 0.0;
+            C vs = 0, va = 0;
             if (c < q && p < r1) {
-                vs = __ldg(col_ptr(S, c) + p);
-                if (with_a) va = __ldg(col_ptr(AS, c) + p);
+                vs = load_col<T0, T12, C>(S, c, p);
+                if (with_a) va = load_col<T0, T12, C>(AS, c, p);
             }
             sS[k * ldsm + c] = vs;
             if (with_a) sA[k * ldsm + c] = va;
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(1024)
         if (active) {
 #pragma unroll 4
             for (int k = grp; k < gs.gk; k += gs.ks) {
-                double a[kTM], b[kTM];
+                C a[kTM], b[kTM];
 #pragma unroll
                 for (int u = 0; u < kTM; ++u) {
                     a[u] = sS[k * ldsm + ti * kTM + u];
@@ -199,17 +216,37 @@ __global__ void __launch_bounds__(1024)
 #pragma unroll
                     for (int v = 0; v < kTM; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
             }
+            if constexpr (std::is_same<C, float>::value) {
+#pragma unroll
+                for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                    for (int v = 0; v < kTM; ++v) {
+                        const C y = acc[u][v] - cmp[u][v];
+                        const C t = tot[u][v] + y;
+                        cmp[u][v] = (t - tot[u][v]) - y;
+                        tot[u][v] = t;
+                        acc[u][v] = C(0);
+                    }
+            }
         }
         __syncthreads();
     }
+    double res[kTM][kTM];
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v) {
+            if constexpr (std::is_same<C, float>::value) res[u][v] = (double)tot[u][v] - (double)cmp[u][v];
+            else res[u][v] = acc[u][v];
+        }
     // add the row groups in order 0, 1, ..., ks-1 (the stage buffers are free now)
     if (gs.ks > 1) {
-        double* red = sm;                          // [ks][nt][16]
+        double* red = reinterpret_cast<double*>(sm_raw);   // [ks][nt][16]
         if (active)
 #pragma unroll
             for (int u = 0; u < kTM; ++u)
 #pragma unroll
-                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = acc[u][v];
+                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
         __syncthreads();
         if (grp == 0) {
 #pragma unroll
@@ -218,7 +255,7 @@ __global__ void __launch_bounds__(1024)
                 for (int v = 0; v < kTM; ++v) {
                     double sum = red[(int64_t)tile * 16 + u * kTM + v];
                     for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
-                    acc[u][v] = sum;
+                    res[u][v] = sum;
                 }
         }
     }
@@ -229,7 +266,7 @@ __global__ void __launch_bounds__(1024)
 #pragma unroll
         for (int v = 0; v < kTM; ++v) {
             const int i = ti * kTM + u, j = tj * kTM + v;
-            if (i < q && j < q) out[i + (int64_t)q * j] = acc[u][v];
+            if (i < q && j < q) out[i + (int64_t)q * j] = res[u][v];
         }
 }
 
@@ -275,37 +312,49 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
 // ------------------------------------------------------------------ Ritz update
 constexpr int kCG = 4;   // output columns per thread
 
+// Pout = S1 C1 + S2 C2 (arithmetic CW, stored TW) and Xout = S0 C0 + Pout (float64).
+// S0 is float64; S1, S2 have type TW.  Each thread owns one grid point and kCG output columns.
+template <typename TW, typename CW>
 __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__ C,
-                         double* Xout, double* Pout, int64_t ldout,
-                         const unsigned* __restrict__ status, unsigned skip) {
-    extern __shared__ double sC[];                 // q x m, column-major
-    if (status && (*status & skip)) return;
+                         double* Xout, TW* Pout, int64_t ldout, const unsigned* __restrict__ status,
+                         unsigned skip) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double* sC = reinterpret_cast<double*>(sm_raw);             // q x m, column-major
     const int q = S.q();
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < q * m; e += 32 * blockDim.y) sC[e] = C[e];
+    CW* sCw = reinterpret_cast<CW*>(sm_raw + sizeof(double) * q * m);   // copy in CW
+    if (status && (*status & skip)) return;
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < q * m; e += 32 * blockDim.y) {
+        sC[e] = C[e];
+        sCw[e] = (CW)C[e];
+    }
     __syncthreads();
     const int c0 = threadIdx.y * kCG;
     const int w0 = S.w[0], w1 = S.w[1], w2 = S.w[2];
     const int64_t ld = S.ld;
+    const double* S0 = static_cast<const double*>(S.p[0]);
+    const TW* S1 = static_cast<const TW*>(S.p[1]);
+    const TW* S2 = static_cast<const TW*>(S.p[2]);
     for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
         const int64_t p = base + threadIdx.x;
         const bool valid = p < n;
-        double accP[kCG], accX[kCG];
+        CW accP[kCG];
+        double accX[kCG];
 #pragma unroll
-        for (int c = 0; c < kCG; ++c) accP[c] = accX[c] = 0.0;
+        for (int c = 0; c < kCG; ++c) { accP[c] = CW(0); accX[c] = 0.0; }
         if (valid) {
             for (int i = 0; i < w1; ++i) {
-                const double v = S.p[1][(int64_t)i * ld + p];
+                const CW v = (CW)ld_as(S1 + (int64_t)i * ld + p);
 #pragma unroll
-                for (int c = 0; c < kCG; ++c) accP[c] = fma(v, sC[(w0 + i) + q * min(c0 + c, m - 1)], accP[c]);
+                for (int c = 0; c < kCG; ++c) accP[c] = fma(v, sCw[(w0 + i) + q * min(c0 + c, m - 1)], accP[c]);
             }
             for (int i = 0; i < w2; ++i) {
-                const double v = S.p[2][(int64_t)i * ld + p];
+                const CW v = (CW)ld_as(S2 + (int64_t)i * ld + p);
 #pragma unroll
                 for (int c = 0; c < kCG; ++c)
-                    accP[c] = fma(v, sC[(w0 + w1 + i) + q * min(c0 + c, m - 1)], accP[c]);
+                    accP[c] = fma(v, sCw[(w0 + w1 + i) + q * min(c0 + c, m - 1)], accP[c]);
             }
             for (int i = 0; i < w0; ++i) {
-                const double v = S.p[0][(int64_t)i * ld + p];
+                const double v = S0[(int64_t)i * ld + p];
 #pragma unroll
                 for (int c = 0; c < kCG; ++c) accX[c] = fma(v, sC[i + q * min(c0 + c, m - 1)], accX[c]);
             }
@@ -315,8 +364,8 @@ __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__
 #pragma unroll
             for (int c = 0; c < kCG; ++c) {
                 if (c0 + c < m) {
-                    Pout[(int64_t)(c0 + c) * ldout + p] = accP[c];
-                    Xout[(int64_t)(c0 + c) * ldout + p] = accX[c] + accP[c];
+                    if (Pout) st_as(Pout + (int64_t)(c0 + c) * ldout + p, accP[c]);
+                    Xout[(int64_t)(c0 + c) * ldout + p] = accX[c] + (double)accP[c];
                 }
             }
         }
@@ -325,24 +374,27 @@ __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__
 
 // V <- V Rinv with Rinv upper triangular (b x b, column-major): each thread owns one grid point
 // and kCG output columns c0..c0+kCG-1, so it needs input columns 0..c0+kCG-1 only.
-__global__ void k_apply_upper(int64_t n, int b, const double* Vin, int64_t ldin, double* Vout,
-                              int64_t ldout, const double* __restrict__ Rinv,
-                              const unsigned* __restrict__ status, unsigned skip) {
-    extern __shared__ double sR[];
+template <typename T>
+__global__ void k_apply_upper(int64_t n, int b, const T* Vin, int64_t ldin, T* Vout, int64_t ldout,
+                              const double* __restrict__ Rinv, const unsigned* __restrict__ status,
+                              unsigned skip) {
+    using C = typename Acc<T>::type;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sR = reinterpret_cast<C*>(sm_raw);
     if (status && (*status & skip)) return;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < b * b; e += 32 * blockDim.y) sR[e] = Rinv[e];
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < b * b; e += 32 * blockDim.y) sR[e] = (C)Rinv[e];
     __syncthreads();
     const int c0 = threadIdx.y * kCG;
     const int iend = min(b, c0 + kCG);
     for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
         const int64_t p = base + threadIdx.x;
         const bool valid = p < n;
-        double acc[kCG];
+        C acc[kCG];
 #pragma unroll
-        for (int c = 0; c < kCG; ++c) acc[c] = 0.0;
+        for (int c = 0; c < kCG; ++c) acc[c] = C(0);
         if (valid) {
             for (int i = 0; i < iend; ++i) {
-                const double v = Vin[(int64_t)i * ldin + p];
+                const C v = (C)Vin[(int64_t)i * ldin + p];
 #pragma unroll
                 for (int c = 0; c < kCG; ++c) acc[c] = fma(v, sR[i + b * min(c0 + c, b - 1)], acc[c]);
             }
@@ -351,7 +403,7 @@ __global__ void k_apply_upper(int64_t n, int b, const double* Vin, int64_t ldin,
         if (valid) {
 #pragma unroll
             for (int c = 0; c < kCG; ++c)
-                if (c0 + c < b) Vout[(int64_t)(c0 + c) * ldout + p] = acc[c];
+                if (c0 + c < b) Vout[(int64_t)(c0 + c) * ldout + p] = (T)acc[c];
         }
     }
 }
@@ -370,13 +422,18 @@ int residual_chunks(int64_t n) {
 }
 
 void launch_residual(int64_t n, const ColList& cols, const double* X, const double* AX, int64_t ld,
-                     const double* lambda, double* W, int64_t ldw, double* partial, cudaStream_t st) {
+                     const double* lambda, DType tw, void* W, int64_t ldw, double* partial,
+                     cudaStream_t st) {
     if (cols.n <= 0) return;
     const int nchunks = residual_chunks(n);
     const int64_t rows = ceil_div(n, nchunks);
     dim3 grid((unsigned)nchunks, (unsigned)cols.n);
-    k_residual<<<grid, kResThreads, 0, st>>>(n, rows, cols, X, AX, ld, lambda, W, ldw, partial,
-                                             nchunks);
+    if (tw == DT_F32)
+        k_residual<float><<<grid, kResThreads, 0, st>>>(n, rows, cols, X, AX, ld, lambda, (float*)W, ldw,
+                                                        partial, nchunks);
+    else
+        k_residual<double><<<grid, kResThreads, 0, st>>>(n, rows, cols, X, AX, ld, lambda, (double*)W, ldw,
+                                                         partial, nchunks);
     LG_CHECK_LAUNCH();
 }
 
@@ -393,21 +450,32 @@ int gram_parts(int64_t n) {
 
 int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n) * 2 * q * q; }
 
-void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
-                 cudaStream_t st) {
+template <typename T0, typename T12, typename C>
+static void gram_t(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
+                   cudaStream_t st) {
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
-    const GramShape gs = gram_shape(S, AS != nullptr);
+    const GramShape gs = gram_shape(S, AS != nullptr, (int)sizeof(C));
     const int nt = gs.ntA + gs.ntB;
     const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
-    LG_REQUIRE(threads <= 1024, LOBPCG_ERR_ARG, "Gram basis too wide");
-    const size_t stage = 2 * (size_t)gs.gk * (T * kTM + 1);
-    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 : 0;
-    const size_t smem = std::max(stage, red) * sizeof(double);
+    LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
+    const size_t stage = 2 * (size_t)gs.gk * (T * kTM + 1) * sizeof(C);
+    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
+    const size_t smem = std::max(stage, red);
     LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
     const int64_t rows = ceil_div(n, nparts);
     Blocks3 A = AS ? *AS : S;
-    k_gram<<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
+    k_gram<T0, T12, C><<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
+}
+
+void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
+                 cudaStream_t st) {
+    const bool has12 = S.w[1] + S.w[2] > 0;
+    const DType t12 = has12 ? S.t12 : S.t0;
+    if (S.t0 == DT_F64 && t12 == DT_F64) gram_t<double, double, double>(n, S, AS, part, nparts, st);
+    else if (S.t0 == DT_F64 && t12 == DT_F32) gram_t<double, float, float>(n, S, AS, part, nparts, st);
+    else if (S.t0 == DT_F32 && t12 == DT_F32) gram_t<float, float, float>(n, S, AS, part, nparts, st);
+    else throw Error(LOBPCG_ERR_ARG, "unsupported Gram block types");
     LG_CHECK_LAUNCH();
 }
 
@@ -424,24 +492,35 @@ void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, do
     LG_CHECK_LAUNCH();
 }
 
-void launch_apply_rinv(int64_t n, int b, const double* Vin, int64_t ldin, double* Vout,
+void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void* Vout,
                        int64_t ldout, const double* Rinv, const unsigned* status,
                        unsigned skip_mask, cudaStream_t st) {
     if (b <= 0) return;
     const int groups = (int)ceil_div(b, kCG);
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
-    k_apply_upper<<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(double), st>>>(
-        n, b, Vin, ldin, Vout, ldout, Rinv, status, skip_mask);
+    if (t == DT_F32)
+        k_apply_upper<float><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(float), st>>>(
+            n, b, (const float*)Vin, ldin, (float*)Vout, ldout, Rinv, status, skip_mask);
+    else
+        k_apply_upper<double><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(double), st>>>(
+            n, b, (const double*)Vin, ldin, (double*)Vout, ldout, Rinv, status, skip_mask);
     LG_CHECK_LAUNCH();
 }
 
-void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout, double* Pout,
+void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout, void* Pout,
                    int64_t ldout, const unsigned* status, unsigned skip_mask, cudaStream_t st) {
     const int groups = (int)ceil_div(m, kCG);
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
-    const size_t smem = (size_t)S.q() * m * sizeof(double);
-    k_update<<<(unsigned)blocks, dim3(32, groups), smem, st>>>(n, m, S, C, Xout, Pout, ldout, status,
-                                                               skip_mask);
+    const bool f32 = (S.w[1] + S.w[2] > 0 ? S.t12 : DT_F64) == DT_F32;
+    if (f32) {
+        const size_t smem = (size_t)S.q() * m * (sizeof(double) + sizeof(float));
+        k_update<float, float><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
+            n, m, S, C, Xout, (float*)Pout, ldout, status, skip_mask);
+    } else {
+        const size_t smem = (size_t)S.q() * m * (2 * sizeof(double));
+        k_update<double, double><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
+            n, m, S, C, Xout, (double*)Pout, ldout, status, skip_mask);
+    }
     LG_CHECK_LAUNCH();
 }
 

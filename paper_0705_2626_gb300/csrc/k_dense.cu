@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kRRThreads)
     __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1];
     __shared__ int ord[kMaxQ + 1], perm[kMaxQ];
     __shared__ int flag, rotated;
+    __shared__ double jthr;
     if (status && (*status & skip)) return;
     double* Linv = work;                       // q x q row-major (ld q)
     double* T1 = work + (int64_t)q * q;        // q x q row-major
@@ -192,10 +193,27 @@ __global__ void __launch_bounds__(kRRThreads)
         }
         V[i * ld + j] = (i == j) ? 1.0 : 0.0;
     }
-    // ---- cyclic Jacobi, round-robin ordering over qe = nq rounded up to even
+    // ---- cyclic Jacobi, round-robin ordering over qe = nq rounded up to even.  A pair is
+    // rotated while |M_pr| > eps ||M||_F: the backward-stable threshold (a relative test against
+    // sqrt(|M_pp M_rr|) would chase the eps ||M|| noise that every rotation leaves behind).
     const int qe = nq + (nq & 1);
     const int npairs = qe / 2;
     for (int i = tid; i < qe; i += blockDim.x) ord[i] = i;
+    {
+        double ss = 0.0;
+        for (int e = tid; e < nq * nq; e += blockDim.x) {
+            const double v = M[(e / nq) * ld + e % nq];
+            ss = fma(v, v, ss);
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+        if ((tid & 31) == 0) rc[tid >> 5] = ss;   // rc is free until the sweeps start
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += rc[w];
+            jthr = kEps * sqrt(t);
+        }
+    }
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (tid == 0) rotated = 0;
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(kRRThreads)
                 double c = 1.0, s = 0.0;
                 if (r < nq) {
                     const double apq = M[p * ld + r], app = M[p * ld + p], arr = M[r * ld + r];
-                    if (fabs(apq) > kEps * sqrt(fabs(app * arr)) && apq != 0.0) {
+                    if (fabs(apq) > jthr) {
                         const double tau = (arr - app) / (2.0 * apq);
                         const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
                         c = 1.0 / sqrt(fma(t, t, 1.0));

@@ -12,9 +12,13 @@
 //     residual        res = r - A e = -6s e + s nb(e) + r
 // Layout: column-major blocks, point p = i + nx*(j + ny*k).  Each thread owns one (i, j)
 // line and marches along k over a chunk of planes, carrying the k-1, k, k+1 values in
-// registers; in-plane neighbours come through L1.  In float64 the sweep is bound by the
-// FP64 pipe (7-8 FP64 instructions per point), not by HBM.
+// registers; in-plane neighbours come through L1.  Storage is float64, float32 or bfloat16;
+// arithmetic is float64 for float64 data (bound by GB300's FP64 pipe, 7-8 instructions per
+// point) and float32 otherwise (bound by HBM).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "dtype.cuh"
 
 namespace lg {
 namespace {
@@ -23,11 +27,12 @@ constexpr int kTX = 32, kTY = 4;
 
 __host__ __device__ inline int zchunk_for(int nz) { return nz >= 64 ? 16 : (nz >= 16 ? 8 : nz); }
 
-template <bool HAS_Z>
+template <typename T, bool HAS_Z>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_stencil_axpby(Grid3 g, int zchunk, int nzc, double a, double b, const double* __restrict__ x,
-                    int64_t ldx, double c, const double* __restrict__ z, int64_t ldz,
-                    double* __restrict__ y, int64_t ldy) {
+    k_stencil_axpby(Grid3 g, int zchunk, int nzc, typename Acc<T>::type a, typename Acc<T>::type b,
+                    const T* __restrict__ x, int64_t ldx, typename Acc<T>::type c,
+                    const T* __restrict__ z, int64_t ldz, T* __restrict__ y, int64_t ldy) {
+    using C = typename Acc<T>::type;
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int col = blockIdx.z / nzc;
@@ -36,23 +41,23 @@ __global__ void __launch_bounds__(kTX* kTY)
     const int k0 = kc * zchunk;
     const int k1 = min(k0 + zchunk, g.nz);
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    const double* xc = x + (int64_t)col * ldx;
-    const double* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
-    double* yc = y + (int64_t)col * ldy;
+    const T* xc = x + (int64_t)col * ldx;
+    const T* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
+    T* yc = y + (int64_t)col * ldy;
     int64_t p = i + sy * (j + (int64_t)g.ny * k0);
-    double xm = (k0 > 0) ? __ldg(xc + p - sz) : 0.0;
-    double x0 = __ldg(xc + p);
+    C xm = (k0 > 0) ? ld_as(xc + p - sz) : C(0);
+    C x0 = ld_as(xc + p);
     const bool hasl = i > 0, hasr = i + 1 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
     for (int k = k0; k < k1; ++k, p += sz) {
-        const double xp = (k + 1 < g.nz) ? __ldg(xc + p + sz) : 0.0;
-        double nb = xm + xp;
-        if (hasl) nb += __ldg(xc + p - 1);
-        if (hasr) nb += __ldg(xc + p + 1);
-        if (hasd) nb += __ldg(xc + p - sy);
-        if (hasu) nb += __ldg(xc + p + sy);
-        double v = fma(b, nb, a * x0);
-        if (HAS_Z) v = fma(c, __ldg(zc + p), v);
-        yc[p] = v;
+        const C xp = (k + 1 < g.nz) ? ld_as(xc + p + sz) : C(0);
+        C nb = xm + xp;
+        if (hasl) nb += ld_as(xc + p - 1);
+        if (hasr) nb += ld_as(xc + p + 1);
+        if (hasd) nb += ld_as(xc + p - sy);
+        if (hasu) nb += ld_as(xc + p + sy);
+        C v = fma(b, nb, a * x0);
+        if (HAS_Z) v = fma(c, ld_as(zc + p), v);
+        st_as(yc + p, v);
         xm = x0;
         x0 = xp;
     }
@@ -60,35 +65,37 @@ __global__ void __launch_bounds__(kTX* kTY)
 
 // Full weighting: coarse point (I, J, K) (0-based) sits on fine (2I+1, 2J+1, 2K+1);
 // weights 1, 1/2 per axis for offsets 0, +-1, overall factor 1/8 (R = P^T / 8).
+template <typename TF, typename TC>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_restrict(Grid3 gf, Grid3 gc, const double* __restrict__ rf, int64_t ldf,
-               double* __restrict__ rc, int64_t ldc) {
+    k_restrict(Grid3 gf, Grid3 gc, const TF* __restrict__ rf, int64_t ldf, TC* __restrict__ rc,
+               int64_t ldc) {
+    using C = typename Acc<TF>::type;
     const int I = blockIdx.x * kTX + threadIdx.x;
     const int J = blockIdx.y * kTY + threadIdx.y;
     const int col = blockIdx.z / gc.nz;
     const int K = blockIdx.z - col * gc.nz;
     if (I >= gc.nx || J >= gc.ny) return;
-    const double* f = rf + (int64_t)col * ldf;
+    const TF* f = rf + (int64_t)col * ldf;
     const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
-    double s = 0.0;
+    C s = 0;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
         const int kk = fk + dz;
         if (kk >= gf.nz) continue;
-        const double wz = dz == 0 ? 1.0 : 0.5;
+        const C wz = dz == 0 ? C(1) : C(0.5);
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const int jj = fj + dy;
             if (jj >= gf.ny) continue;
-            const double wzy = wz * (dy == 0 ? 1.0 : 0.5);
+            const C wzy = wz * (dy == 0 ? C(1) : C(0.5));
             const int64_t row = (int64_t)gf.nx * (jj + (int64_t)gf.ny * kk);
-            double t = __ldg(f + row + fi);
-            if (fi - 1 >= 0) t = fma(0.5, __ldg(f + row + fi - 1), t);
-            if (fi + 1 < gf.nx) t = fma(0.5, __ldg(f + row + fi + 1), t);
+            C t = ld_as(f + row + fi);
+            if (fi - 1 >= 0) t = fma(C(0.5), ld_as(f + row + fi - 1), t);
+            if (fi + 1 < gf.nx) t = fma(C(0.5), ld_as(f + row + fi + 1), t);
             s = fma(wzy, t, s);
         }
     }
-    rc[(int64_t)col * ldc + I + (int64_t)gc.nx * (J + (int64_t)gc.ny * K)] = 0.125 * s;
+    st_as(rc + (int64_t)col * ldc + I + (int64_t)gc.nx * (J + (int64_t)gc.ny * K), C(0.125) * s);
 }
 
 // Trilinear prolongation: fine index f (1-based) takes coarse f/2 with weight 1 when f is
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(kTX* kTY)
 // and nc+1 are boundary zeros.
 struct Taps {
     int idx[2];
-    double w[2];
+    float w[2];
     int n;
 };
 __device__ inline Taps taps1d(int f0, int nc) {
@@ -105,34 +112,37 @@ __device__ inline Taps taps1d(int f0, int nc) {
     t.n = 0;
     if ((f & 1) == 0) {
         const int I = f >> 1;
-        if (I <= nc) { t.idx[t.n] = I - 1; t.w[t.n] = 1.0; ++t.n; }
+        if (I <= nc) { t.idx[t.n] = I - 1; t.w[t.n] = 1.0f; ++t.n; }
     } else {
         const int I1 = (f - 1) >> 1, I2 = (f + 1) >> 1;
-        if (I1 >= 1) { t.idx[t.n] = I1 - 1; t.w[t.n] = 0.5; ++t.n; }
-        if (I2 <= nc) { t.idx[t.n] = I2 - 1; t.w[t.n] = 0.5; ++t.n; }
+        if (I1 >= 1) { t.idx[t.n] = I1 - 1; t.w[t.n] = 0.5f; ++t.n; }
+        if (I2 <= nc) { t.idx[t.n] = I2 - 1; t.w[t.n] = 0.5f; ++t.n; }
     }
     return t;
 }
 
+template <typename TC, typename TF>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_prolong_add(Grid3 gf, Grid3 gc, const double* __restrict__ ec, int64_t ldc,
-                  double* __restrict__ ef, int64_t ldf) {
+    k_prolong_add(Grid3 gf, Grid3 gc, const TC* __restrict__ ec, int64_t ldc, TF* __restrict__ ef,
+                  int64_t ldf) {
+    using C = typename Acc<TF>::type;
     const int i = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
     const int col = blockIdx.z / gf.nz;
     const int k = blockIdx.z - col * gf.nz;
     if (i >= gf.nx || j >= gf.ny) return;
-    const double* c = ec + (int64_t)col * ldc;
+    const TC* c = ec + (int64_t)col * ldc;
     const Taps tx = taps1d(i, gc.nx), ty = taps1d(j, gc.ny), tz = taps1d(k, gc.nz);
-    double s = 0.0;
+    C s = 0;
     for (int a = 0; a < tz.n; ++a)
         for (int b = 0; b < ty.n; ++b) {
-            const double w = tz.w[a] * ty.w[b];
+            const C w = C(tz.w[a]) * C(ty.w[b]);
             const int64_t row = (int64_t)gc.nx * (ty.idx[b] + (int64_t)gc.ny * tz.idx[a]);
-            for (int d = 0; d < tx.n; ++d) s = fma(w * tx.w[d], __ldg(c + row + tx.idx[d]), s);
+            for (int d = 0; d < tx.n; ++d) s = fma(w * C(tx.w[d]), C(ld_as(c + row + tx.idx[d])), s);
         }
     const int64_t p = (int64_t)col * ldf + i + (int64_t)gf.nx * (j + (int64_t)gf.ny * k);
-    ef[p] += s;
+    const C old = ld_as(ef + p);
+    st_as(ef + p, old + s);
 }
 
 // Coarsest-level exact solve.  The 7-point Dirichlet operator s*(6u - nb) on an
@@ -184,8 +194,9 @@ __device__ void sine_pass(const Grid3& g, int ax, const double* __restrict__ Q,
     __syncthreads();
 }
 
-__global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const double* __restrict__ r,
-                               int64_t ldr, double* __restrict__ e, int64_t lde) {
+template <typename T>
+__global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const T* __restrict__ r,
+                               int64_t ldr, T* __restrict__ e, int64_t lde) {
     extern __shared__ double sm[];
     const int n = g.nx * g.ny * g.nz;
     double* u = sm;
@@ -195,7 +206,7 @@ __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const do
     const double* Qz = Qy + g.ny * g.ny;
     const double* lam = Qz + g.nz * g.nz;
     const int col = blockIdx.x;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) u[p] = r[(int64_t)col * ldr + p];
+    for (int p = threadIdx.x; p < n; p += blockDim.x) u[p] = (double)ld_as(r + (int64_t)col * ldr + p);
     __syncthreads();
     sine_pass(g, 0, Qx, u, v);
     sine_pass(g, 1, Qy, v, u);
@@ -205,40 +216,89 @@ __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const do
     sine_pass(g, 0, Qx, v, u);
     sine_pass(g, 1, Qy, u, v);
     sine_pass(g, 2, Qz, v, u);
-    for (int p = threadIdx.x; p < n; p += blockDim.x) e[(int64_t)col * lde + p] = u[p];
+    for (int p = threadIdx.x; p < n; p += blockDim.x) st_as(e + (int64_t)col * lde + p, u[p]);
 }
 
-}  // namespace
+template <typename TS, typename TD>
+__global__ void k_convert(int64_t n, int ncols, const TS* __restrict__ src, int64_t lds,
+                          TD* __restrict__ dst, int64_t ldd) {
+    const int64_t total = n * ncols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / n, p = t - j * n;
+        st_as(dst + j * ldd + p, ld_as(src + j * lds + p));
+    }
+}
 
-void launch_stencil_axpby(const Grid3& g, int ncols, double a, double b, const double* x,
-                          int64_t ldx, double c, const double* z, int64_t ldz, double* y,
-                          int64_t ldy, cudaStream_t st) {
-    if (ncols <= 0 || g.n() == 0) return;
+template <typename T>
+void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int64_t ldx, double c,
+               const void* z, int64_t ldz, void* y, int64_t ldy, cudaStream_t st) {
+    using C = typename Acc<T>::type;
     const int zc = zchunk_for(g.nz);
     const int nzc = (int)ceil_div(g.nz, zc);
     dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
     dim3 block(kTX, kTY);
     if (z)
-        k_stencil_axpby<true><<<grid, block, 0, st>>>(g, zc, nzc, a, b, x, ldx, c, z, ldz, y, ldy);
+        k_stencil_axpby<T, true><<<grid, block, 0, st>>>(g, zc, nzc, (C)a, (C)b, (const T*)x, ldx, (C)c,
+                                                         (const T*)z, ldz, (T*)y, ldy);
     else
-        k_stencil_axpby<false><<<grid, block, 0, st>>>(g, zc, nzc, a, b, x, ldx, 0.0, nullptr, 0, y,
-                                                       ldy);
-    LG_CHECK_LAUNCH();
+        k_stencil_axpby<T, false><<<grid, block, 0, st>>>(g, zc, nzc, (C)a, (C)b, (const T*)x, ldx, C(0),
+                                                          nullptr, 0, (T*)y, ldy);
 }
 
-void launch_restrict(const Grid3& gf, const Grid3& gc, int ncols, const double* rf, int64_t ldf,
-                     double* rc, int64_t ldc, cudaStream_t st) {
-    if (ncols <= 0) return;
+template <typename TF, typename TC>
+void restrict_t(const Grid3& gf, const Grid3& gc, int ncols, const void* rf, int64_t ldf, void* rc,
+                int64_t ldc, cudaStream_t st) {
     dim3 grid((unsigned)ceil_div(gc.nx, kTX), (unsigned)ceil_div(gc.ny, kTY), (unsigned)(gc.nz * ncols));
-    k_restrict<<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, rf, ldf, rc, ldc);
+    k_restrict<TF, TC><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, (const TF*)rf, ldf, (TC*)rc, ldc);
+}
+
+template <typename TC, typename TF>
+void prolong_t(const Grid3& gf, const Grid3& gc, int ncols, const void* ec, int64_t ldc, void* ef,
+               int64_t ldf, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(gf.nx, kTX), (unsigned)ceil_div(gf.ny, kTY), (unsigned)(gf.nz * ncols));
+    k_prolong_add<TC, TF><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, (const TC*)ec, ldc, (TF*)ef, ldf);
+}
+
+template <typename TS, typename TD>
+void convert_t(int64_t n, int ncols, const void* src, int64_t lds, void* dst, int64_t ldd, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(n * ncols, 256), (int64_t)kNumSMs * 16);
+    k_convert<TS, TD><<<(unsigned)blocks, 256, 0, st>>>(n, ncols, (const TS*)src, lds, (TD*)dst, ldd);
+}
+
+}  // namespace
+
+void launch_stencil_axpby(const Grid3& g, int ncols, DType t, double a, double b, const void* x,
+                          int64_t ldx, double c, const void* z, int64_t ldz, void* y,
+                          int64_t ldy, cudaStream_t st) {
+    if (ncols <= 0 || g.n() == 0) return;
+    switch (t) {
+        case DT_F64: stencil_t<double>(g, ncols, a, b, x, ldx, c, z, ldz, y, ldy, st); break;
+        case DT_F32: stencil_t<float>(g, ncols, a, b, x, ldx, c, z, ldz, y, ldy, st); break;
+        case DT_BF16: stencil_t<__nv_bfloat16>(g, ncols, a, b, x, ldx, c, z, ldz, y, ldy, st); break;
+    }
     LG_CHECK_LAUNCH();
 }
 
-void launch_prolong_add(const Grid3& gf, const Grid3& gc, int ncols, const double* ec,
-                        int64_t ldc, double* ef, int64_t ldf, cudaStream_t st) {
+void launch_restrict(const Grid3& gf, const Grid3& gc, int ncols, DType tf, const void* rf,
+                     int64_t ldf, DType tc, void* rc, int64_t ldc, cudaStream_t st) {
     if (ncols <= 0) return;
-    dim3 grid((unsigned)ceil_div(gf.nx, kTX), (unsigned)ceil_div(gf.ny, kTY), (unsigned)(gf.nz * ncols));
-    k_prolong_add<<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, ec, ldc, ef, ldf);
+    if (tf == DT_F64 && tc == DT_F64) restrict_t<double, double>(gf, gc, ncols, rf, ldf, rc, ldc, st);
+    else if (tf == DT_F32 && tc == DT_BF16) restrict_t<float, __nv_bfloat16>(gf, gc, ncols, rf, ldf, rc, ldc, st);
+    else if (tf == DT_F32 && tc == DT_F32) restrict_t<float, float>(gf, gc, ncols, rf, ldf, rc, ldc, st);
+    else if (tf == DT_BF16 && tc == DT_BF16) restrict_t<__nv_bfloat16, __nv_bfloat16>(gf, gc, ncols, rf, ldf, rc, ldc, st);
+    else throw Error(LOBPCG_ERR_ARG, "unsupported restriction types");
+    LG_CHECK_LAUNCH();
+}
+
+void launch_prolong_add(const Grid3& gf, const Grid3& gc, int ncols, DType tc, const void* ec,
+                        int64_t ldc, DType tf, void* ef, int64_t ldf, cudaStream_t st) {
+    if (ncols <= 0) return;
+    if (tc == DT_F64 && tf == DT_F64) prolong_t<double, double>(gf, gc, ncols, ec, ldc, ef, ldf, st);
+    else if (tc == DT_BF16 && tf == DT_F32) prolong_t<__nv_bfloat16, float>(gf, gc, ncols, ec, ldc, ef, ldf, st);
+    else if (tc == DT_F32 && tf == DT_F32) prolong_t<float, float>(gf, gc, ncols, ec, ldc, ef, ldf, st);
+    else if (tc == DT_BF16 && tf == DT_BF16) prolong_t<__nv_bfloat16, __nv_bfloat16>(gf, gc, ncols, ec, ldc, ef, ldf, st);
+    else throw Error(LOBPCG_ERR_ARG, "unsupported prolongation types");
     LG_CHECK_LAUNCH();
 }
 
@@ -252,17 +312,36 @@ void launch_coarse_setup(const Grid3& g, double scale, double* tables, cudaStrea
     LG_CHECK_LAUNCH();
 }
 
-void launch_coarse_solve(const Grid3& g, int ncols, const double* tables, const double* r,
-                         int64_t ldr, double* e, int64_t lde, cudaStream_t st) {
+void launch_coarse_solve(const Grid3& g, int ncols, DType t, const double* tables, const void* r,
+                         int64_t ldr, void* e, int64_t lde, cudaStream_t st) {
     if (ncols <= 0) return;
     const size_t smem = 2 * (size_t)g.n() * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        LG_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * 4096 * (int)sizeof(double)));
-        attr_set = true;
+    const int maxsmem = 2 * 4096 * (int)sizeof(double);
+    int dev = 0;
+    LG_CUDA(cudaGetDevice(&dev));
+    static bool attr_set[64][3] = {};
+    if (dev < 64 && !attr_set[dev][t]) {
+        if (t == DT_F64) LG_CUDA(cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+        if (t == DT_F32) LG_CUDA(cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+        if (t == DT_BF16) LG_CUDA(cudaFuncSetAttribute(k_coarse_solve<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+        attr_set[dev][t] = true;
     }
-    k_coarse_solve<<<ncols, 256, smem, st>>>(g, tables, r, ldr, e, lde);
+    switch (t) {
+        case DT_F64: k_coarse_solve<double><<<ncols, 256, smem, st>>>(g, tables, (const double*)r, ldr, (double*)e, lde); break;
+        case DT_F32: k_coarse_solve<float><<<ncols, 256, smem, st>>>(g, tables, (const float*)r, ldr, (float*)e, lde); break;
+        case DT_BF16: k_coarse_solve<__nv_bfloat16><<<ncols, 256, smem, st>>>(g, tables, (const __nv_bfloat16*)r, ldr, (__nv_bfloat16*)e, lde); break;
+    }
+    LG_CHECK_LAUNCH();
+}
+
+void launch_convert(int64_t n, int ncols, DType ts, const void* src, int64_t lds, DType td,
+                    void* dst, int64_t ldd, cudaStream_t st) {
+    if (ncols <= 0 || n <= 0) return;
+    if (ts == DT_F64 && td == DT_F32) convert_t<double, float>(n, ncols, src, lds, dst, ldd, st);
+    else if (ts == DT_F32 && td == DT_F64) convert_t<float, double>(n, ncols, src, lds, dst, ldd, st);
+    else if (ts == DT_F32 && td == DT_F32) convert_t<float, float>(n, ncols, src, lds, dst, ldd, st);
+    else if (ts == DT_F64 && td == DT_F64) convert_t<double, double>(n, ncols, src, lds, dst, ldd, st);
+    else throw Error(LOBPCG_ERR_ARG, "unsupported conversion");
     LG_CHECK_LAUNCH();
 }
 

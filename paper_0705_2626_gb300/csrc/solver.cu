@@ -7,6 +7,13 @@
 // the host only keeps the active index set J, which needs the b residual norms of each
 // iteration (one device-to-host copy per iteration, together with a status word that the small
 // dense kernels use to report breakdowns).  Nothing on the iteration path falls back to the CPU.
+//
+// Two forms.  LOBPCG_FP64: every block and every operation in float64.  LOBPCG_MIXED: X, AX and
+// all small matrices in float64; W, AW, P, AP, the V-cycle's finest level in float32 and its
+// coarser levels stored in bfloat16; the Gram products in float32 with compensated sums.  When
+// every implicit residual passes, a float64 correction sweep (steps 3-4 applied to the current X
+// with a fresh float64 A X) recomputes the Ritz pairs and their residuals; columns that fail
+// re-enter the loop.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -20,20 +27,20 @@ using namespace lg;
 
 namespace lg {
 std::atomic<long long> g_kernel_launches{0};
-}
+thread_local std::string g_handle_free_error;
+}  // namespace lg
 
 namespace {
 
-struct DBuf {
-    double* p = nullptr;
+struct Buf {
+    void* p = nullptr;
     size_t bytes = 0;
 };
+inline double* f64(const Buf& b) { return static_cast<double*>(b.p); }
+
+constexpr int kMaxFp64Sweeps = 8;
 
 }  // namespace
-
-namespace lg {
-thread_local std::string g_handle_free_error;
-}
 
 struct lobpcg_handle {
     int device = 0;
@@ -41,6 +48,8 @@ struct lobpcg_handle {
     lobpcg_allocator alloc{};
     bool has_alloc = false;
     int precision = LOBPCG_FP64;
+    DType tw = DT_F64;      // W / P family and V-cycle level 0
+    DType tl = DT_F64;      // V-cycle levels >= 1
     std::string err;
     bool poisoned = false;
 
@@ -54,25 +63,26 @@ struct lobpcg_handle {
     double omega = 2.0 / 3.0;
     std::vector<Grid3> lv;
     std::vector<double> lscale;
-    DBuf coarse_tab;
+    Buf coarse_tab;
     // options
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
 
     // workspace for a block of wm columns
     int wm = 0;
     int64_t ld = 0;
-    DBuf X, AX, W, AW, P, AP, Pc, APc, E0, T0;
-    std::vector<DBuf> lr, le, lt;
+    Buf X, AX;                                  // float64
+    Buf W, AW, P, AP, Pc, APc, E0, T0;          // type tw
+    std::vector<Buf> lr, le, lt;                // type tl
     std::vector<int64_t> lld;
-    DBuf part;          // Gram / residual partial sums
-    DBuf small;         // gramA, gramB, C, lam, Rinv, norms, rr work
+    Buf part;          // Gram / residual partial sums
+    Buf small;         // gramA, gramB, C, lam, Rinv, norms, rr work
     unsigned* status = nullptr;
     size_t part_doubles = 0;
     double *gramA = nullptr, *gramB = nullptr, *Cm = nullptr, *lam = nullptr, *Rinv = nullptr,
            *norms = nullptr, *rrwork = nullptr, *Gsmall = nullptr;
 
     // user initial block
-    DBuf X0;
+    Buf X0;
     int X0_m = 0;
 
     // solve state
@@ -84,10 +94,10 @@ struct lobpcg_handle {
     std::vector<int> J;
     std::vector<double> lam_h, norms_h, resid_h;
     int p_dropped = 0;
+    int fp64_sweeps = 0;
     double setup_ms = 0.0, solve_ms = 0.0;
     double phase_ms[LOBPCG_NPHASES] = {};
     cudaEvent_t ev[LOBPCG_NPHASES + 2] = {};
-    int last_status = LOBPCG_OK;
     long long launches_at_start = 0;
 };
 
@@ -110,7 +120,7 @@ void* dalloc(lobpcg_t* h, size_t bytes) {
     return p;
 }
 
-void dfree(lobpcg_t* h, DBuf& b) {
+void dfree(lobpcg_t* h, Buf& b) {
     if (b.p) {
         if (h->has_alloc) h->alloc.free(h->alloc.ctx, b.p, b.bytes, (void*)h->stream);
         else cudaFreeAsync(b.p, h->stream);
@@ -119,18 +129,18 @@ void dfree(lobpcg_t* h, DBuf& b) {
     b.bytes = 0;
 }
 
-void ensure(lobpcg_t* h, DBuf& b, size_t bytes) {
+void ensure(lobpcg_t* h, Buf& b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return;
     dfree(h, b);
-    b.p = (double*)dalloc(h, bytes);
+    b.p = dalloc(h, bytes);
     b.bytes = bytes;
 }
 
 int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 void free_workspace(lobpcg_t* h) {
-    for (DBuf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0,
-                    &h->part, &h->small})
+    for (Buf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0,
+                   &h->part, &h->small})
         dfree(h, *b);
     for (auto& b : h->lr) dfree(h, b);
     for (auto& b : h->le) dfree(h, b);
@@ -149,17 +159,19 @@ void ensure_workspace(lobpcg_t* h, int wm) {
     h->state = 0;   // a finished or running solve does not survive a reallocation
     const int64_t n = h->g.n();
     h->ld = round_up(n, 32);
-    const size_t blk = (size_t)h->ld * wm * sizeof(double);
-    for (DBuf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0})
-        ensure(h, *b, blk);
+    const size_t blk64 = (size_t)h->ld * wm * sizeof(double);
+    const size_t blkw = (size_t)h->ld * wm * dtype_size(h->tw);
+    ensure(h, h->X, blk64);
+    ensure(h, h->AX, blk64);
+    for (Buf* b : {&h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0}) ensure(h, *b, blkw);
     const int L = (int)h->lv.size();
-    h->lr.assign(L, DBuf{});
-    h->le.assign(L, DBuf{});
-    h->lt.assign(L, DBuf{});
+    h->lr.assign(L, Buf{});
+    h->le.assign(L, Buf{});
+    h->lt.assign(L, Buf{});
     h->lld.assign(L, 0);
     for (int l = 1; l < L; ++l) {
         h->lld[l] = round_up(h->lv[l].n(), 32);
-        const size_t bytes = (size_t)h->lld[l] * wm * sizeof(double);
+        const size_t bytes = (size_t)h->lld[l] * wm * dtype_size(h->tl);
         ensure(h, h->lr[l], bytes);
         ensure(h, h->le[l], bytes);
         ensure(h, h->lt[l], bytes);
@@ -171,7 +183,7 @@ void ensure_workspace(lobpcg_t* h, int wm) {
     const size_t nsmall = 2 * (size_t)q * q + (size_t)q * wm + wm + (size_t)wm * wm + wm +
                           (size_t)rr_work_doubles(q) + (size_t)wm * wm + 8;
     ensure(h, h->small, nsmall * sizeof(double));
-    double* s = h->small.p;
+    double* s = f64(h->small);
     h->gramA = s; s += (size_t)q * q;
     h->gramB = s; s += (size_t)q * q;
     h->Cm = s; s += (size_t)q * wm;
@@ -197,79 +209,87 @@ ColList identity_cols(int b) {
 }
 
 // ------------------------------------------------------------------ operator and T
-void spmv(lobpcg_t* h, int ncols, const double* x, int64_t ldx, double* y, int64_t ldy) {
-    launch_stencil_axpby(h->g, ncols, 6.0 * h->scale, -h->scale, x, ldx, 0.0, nullptr, 0, y, ldy,
+void spmv(lobpcg_t* h, int ncols, DType t, const void* x, int64_t ldx, void* y, int64_t ldy) {
+    launch_stencil_axpby(h->g, ncols, t, 6.0 * h->scale, -h->scale, x, ldx, 0.0, nullptr, 0, y, ldy,
                          h->stream);
 }
 
-void copy_cols(lobpcg_t* h, int ncols, int64_t n, const double* src, int64_t lds, double* dst,
+void copy_cols(lobpcg_t* h, int ncols, int64_t n, DType t, const void* src, int64_t lds, void* dst,
                int64_t ldd) {
-    LG_CUDA(cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double),
-                              n * sizeof(double), ncols, cudaMemcpyDeviceToDevice, h->stream));
+    const size_t es = dtype_size(t);
+    LG_CUDA(cudaMemcpy2DAsync(dst, ldd * es, src, lds * es, n * es, ncols, cudaMemcpyDeviceToDevice,
+                              h->stream));
 }
 
-// V-cycle on level l: e = T_l r for b columns.  tmp is a scratch block of the same shape.
-void vcycle(lobpcg_t* h, int l, int b, const double* r, int64_t ldr, double* e, int64_t lde,
-            double* tmp, int64_t ldt) {
+void* col(const Buf& b, DType t, int64_t ld, int j) {
+    return static_cast<char*>(b.p) + (size_t)j * ld * dtype_size(t);
+}
+
+// V-cycle on level l: e = T_l r for b columns of type t.  tmp is a scratch block of the same shape.
+void vcycle(lobpcg_t* h, int l, int b, DType t, const void* r, int64_t ldr, void* e, int64_t lde,
+            void* tmp, int64_t ldt) {
     const Grid3& g = h->lv[l];
     const int L = (int)h->lv.size();
     const int64_t n = g.n();
     if (l == L - 1) {
-        launch_coarse_solve(g, b, h->coarse_tab.p, r, ldr, e, lde, h->stream);
+        launch_coarse_solve(g, b, t, f64(h->coarse_tab), r, ldr, e, lde, h->stream);
         return;
     }
     const double s = h->lscale[l], w = h->omega, alpha = w / (6.0 * s);
-    double* cur = e;
+    void* cur = e;
     int64_t ldc = lde;
-    double* oth = tmp;
+    void* oth = tmp;
     int64_t ldo = ldt;
     auto swap_bufs = [&]() { std::swap(cur, oth); std::swap(ldc, ldo); };
     // pre-smoothing from e = 0; the first sweep (e = alpha r) folds into the second
     int done = 0;
     if (h->nu_pre >= 2) {
-        launch_stencil_axpby(g, b, alpha * (2.0 - w), alpha * w / 6.0, r, ldr, 0.0, nullptr, 0, cur,
+        launch_stencil_axpby(g, b, t, alpha * (2.0 - w), alpha * w / 6.0, r, ldr, 0.0, nullptr, 0, cur,
                              ldc, h->stream);
         done = 2;
     } else {
-        launch_stencil_axpby(g, b, alpha, 0.0, r, ldr, 0.0, nullptr, 0, cur, ldc, h->stream);
+        launch_stencil_axpby(g, b, t, alpha, 0.0, r, ldr, 0.0, nullptr, 0, cur, ldc, h->stream);
         done = 1;
     }
     for (; done < h->nu_pre; ++done) {
-        launch_stencil_axpby(g, b, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
+        launch_stencil_axpby(g, b, t, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
         swap_bufs();
     }
     // residual r - A e, restricted to level l+1
-    launch_stencil_axpby(g, b, -6.0 * s, s, cur, ldc, 1.0, r, ldr, oth, ldo, h->stream);
+    launch_stencil_axpby(g, b, t, -6.0 * s, s, cur, ldc, 1.0, r, ldr, oth, ldo, h->stream);
     const Grid3& gc = h->lv[l + 1];
-    launch_restrict(g, gc, b, oth, ldo, h->lr[l + 1].p, h->lld[l + 1], h->stream);
-    vcycle(h, l + 1, b, h->lr[l + 1].p, h->lld[l + 1], h->le[l + 1].p, h->lld[l + 1],
+    const DType tc = h->tl;
+    launch_restrict(g, gc, b, t, oth, ldo, tc, h->lr[l + 1].p, h->lld[l + 1], h->stream);
+    vcycle(h, l + 1, b, tc, h->lr[l + 1].p, h->lld[l + 1], h->le[l + 1].p, h->lld[l + 1],
            h->lt[l + 1].p, h->lld[l + 1]);
-    launch_prolong_add(g, gc, b, h->le[l + 1].p, h->lld[l + 1], cur, ldc, h->stream);
-    for (int t = 0; t < h->nu_post; ++t) {
-        launch_stencil_axpby(g, b, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
+    launch_prolong_add(g, gc, b, tc, h->le[l + 1].p, h->lld[l + 1], t, cur, ldc, h->stream);
+    for (int k = 0; k < h->nu_post; ++k) {
+        launch_stencil_axpby(g, b, t, 1.0 - w, w / 6.0, cur, ldc, alpha, r, ldr, oth, ldo, h->stream);
         swap_bufs();
     }
-    if (cur != e) copy_cols(h, b, n, cur, ldc, e, lde);
+    if (cur != e) copy_cols(h, b, n, t, cur, ldc, e, lde);
 }
 
-// e = T r (level 0).  tmp: n-by-b scratch, distinct from r and e.
-void precond(lobpcg_t* h, int b, const double* r, int64_t ldr, double* e, int64_t lde,
-             double* tmp, int64_t ldt) {
+// e = T r (level 0, type t).  tmp: n-by-b scratch of type t, distinct from r and e.
+void precond(lobpcg_t* h, int b, DType t, const void* r, int64_t ldr, void* e, int64_t lde,
+             void* tmp, int64_t ldt) {
     if (h->pc_kind == LOBPCG_PRECOND_NONE) {
-        copy_cols(h, b, h->g.n(), r, ldr, e, lde);
+        copy_cols(h, b, h->g.n(), t, r, ldr, e, lde);
         return;
     }
-    vcycle(h, 0, b, r, ldr, e, lde, tmp, ldt);
+    vcycle(h, 0, b, t, r, ldr, e, lde, tmp, ldt);
 }
 
 // ------------------------------------------------------------------ Gram helpers
-Blocks3 blocks(const double* p0, int w0, const double* p1, int w1, const double* p2, int w2,
-               int64_t ld) {
+Blocks3 blocks(const void* p0, int w0, DType t0, const void* p1, int w1, const void* p2, int w2,
+               DType t12, int64_t ld) {
     Blocks3 b{};
     b.p[0] = p0; b.w[0] = w0;
     b.p[1] = w1 ? p1 : p0; b.w[1] = w1;
     b.p[2] = w2 ? p2 : p0; b.w[2] = w2;
     b.ld = ld;
+    b.t0 = t0;
+    b.t12 = t12;
     return b;
 }
 
@@ -279,8 +299,8 @@ void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* 
     const int q = S.q();
     const int nparts = gram_parts(n);
     LG_REQUIRE((size_t)nparts * 2 * q * q <= h->part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
-    launch_gram(n, S, AS, h->part.p, nparts, h->stream);
-    launch_gram_finalize(q, nparts, h->part.p, AS != nullptr, gA, gB, paper_lam, &S, h->stream);
+    launch_gram(n, S, AS, f64(h->part), nparts, h->stream);
+    launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
 }
 
 // ------------------------------------------------------------------ timing
@@ -305,8 +325,9 @@ void residual_into_W(lobpcg_t* h) {
     ColList cols{};
     cols.n = (int)h->J.size();
     for (int t = 0; t < cols.n; ++t) cols.idx[t] = h->J[t];
-    launch_residual(n, cols, h->X.p, h->AX.p, h->ld, h->lam, h->W.p, h->ld, h->part.p, h->stream);
-    launch_norms_finalize(cols.n, residual_chunks(n), h->part.p, h->norms, h->stream);
+    launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, h->tw, h->W.p, h->ld, f64(h->part),
+                    h->stream);
+    launch_norms_finalize(cols.n, residual_chunks(n), f64(h->part), h->norms, h->stream);
 }
 
 // Copy the small per-iteration results to the host: norms of J, lambda, status word.
@@ -324,6 +345,38 @@ unsigned fetch_small(lobpcg_t* h) {
     return st;
 }
 
+// Steps 3-4 on the current X, all in float64: X = X R^-1 with R = chol(X^T X), AX = A X,
+// (X^T AX) TMP = TMP Lambda, X = X TMP, AX = AX TMP; then step 7 for all m columns.
+// This is the setup of the algorithm and, in the mixed form, the float64 correction sweep.
+void orthonormalize_and_rr(lobpcg_t* h) {
+    const int64_t n = h->g.n();
+    const int m = h->m;
+    cudaStream_t st = h->stream;
+    const Blocks3 SX = blocks(h->X.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
+    gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr);
+    launch_chol_rinv(m, h->Gsmall, h->Rinv, h->status, ST_X_BREAKDOWN, 0u, st);
+    launch_apply_rinv(n, m, DT_F64, h->X.p, h->ld, h->X.p, h->ld, h->Rinv, h->status, ST_X_BREAKDOWN, st);
+    spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
+    const Blocks3 SAX = blocks(h->AX.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
+    gram(h, SX, &SAX, h->gramA, h->gramB, nullptr);
+    launch_rayleigh_ritz(m, m, m, h->gramA, nullptr, h->lam, h->Cm, h->rrwork, h->status,
+                         ST_X_BREAKDOWN, st);
+    const unsigned skip = ST_X_BREAKDOWN | ST_RR_BREAKDOWN;
+    launch_update(n, m, SX, h->Cm, f64(h->X), nullptr, h->ld, h->status, skip, st);
+    launch_update(n, m, SAX, h->Cm, f64(h->AX), nullptr, h->ld, h->status, skip, st);
+    h->J.resize(m);
+    for (int j = 0; j < m; ++j) h->J[j] = j;
+    residual_into_W(h);
+}
+
+void check_setup_status(lobpcg_t* h, unsigned stw) {
+    if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite entry in the block X");
+    if (stw & (ST_X_BREAKDOWN | ST_RR_BREAKDOWN))
+        throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (step 3)");
+    for (double v : h->lam_h)
+        if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value");
+}
+
 void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     require_op(h);
     const int64_t n = h->g.n();
@@ -336,6 +389,7 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     h->tol = tol;
     h->k = 0;
     h->p_dropped = 0;
+    h->fp64_sweeps = 0;
     h->J.clear();
     std::fill(h->phase_ms, h->phase_ms + LOBPCG_NPHASES, 0.0);
     h->state = 0;
@@ -343,37 +397,17 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES], st));
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
     // input block
-    if (h->X0.p && h->X0_m == m) copy_cols(h, m, n, h->X0.p, n, h->X.p, h->ld);
-    else launch_random_block(seed, n, m, h->X.p, h->ld, st);
-    // step 3: X = X R^-1 with R = chol(X^T X); AX = A X
-    const Blocks3 SX = blocks(h->X.p, m, nullptr, 0, nullptr, 0, h->ld);
-    gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr);
-    launch_chol_rinv(m, h->Gsmall, h->Rinv, h->status, ST_X_BREAKDOWN, 0u, st);
-    launch_apply_rinv(n, m, h->X.p, h->ld, h->X.p, h->ld, h->Rinv, h->status,
-                      ST_X_BREAKDOWN, st);
-    spmv(h, m, h->X.p, h->ld, h->AX.p, h->ld);
-    // step 4: (X^T AX) TMP = TMP Lambda; X = X TMP; AX = AX TMP
-    const Blocks3 SAX = blocks(h->AX.p, m, nullptr, 0, nullptr, 0, h->ld);
-    gram(h, SX, &SAX, h->gramA, h->gramB, nullptr);
-    launch_rayleigh_ritz(m, m, m, h->gramA, nullptr, h->lam, h->Cm, h->rrwork, h->status,
-                         ST_X_BREAKDOWN, st);
-    launch_update(n, m, SX, h->Cm, h->X.p, h->P.p, h->ld, h->status, ST_X_BREAKDOWN | ST_RR_BREAKDOWN, st);
-    launch_update(n, m, SAX, h->Cm, h->AX.p, h->AP.p, h->ld, h->status, ST_X_BREAKDOWN | ST_RR_BREAKDOWN, st);
-    // step 5 and step 7 of k = 0
-    h->J.resize(m);
-    for (int j = 0; j < m; ++j) h->J[j] = j;
-    residual_into_W(h);
+    if (h->X0.p && h->X0_m == m) copy_cols(h, m, n, DT_F64, h->X0.p, n, h->X.p, h->ld);
+    else launch_random_block(seed, n, m, f64(h->X), h->ld, st);
+    // steps 3-5 and step 7 of k = 0
+    orthonormalize_and_rr(h);
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], st));
     const unsigned stw = fetch_small(h);
     float ms = 0.f;
     LG_CUDA(cudaEventElapsedTime(&ms, h->ev[LOBPCG_NPHASES], h->ev[LOBPCG_NPHASES + 1]));
     h->setup_ms = ms;
     h->solve_ms = 0.0;
-    if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite entry in the initial block");
-    if (stw & (ST_X_BREAKDOWN | ST_RR_BREAKDOWN))
-        throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (step 3)");
-    for (double v : h->lam_h)
-        if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value at setup");
+    check_setup_status(h, stw);
     h->pending_check = true;
     h->state = 1;
 }
@@ -393,10 +427,11 @@ bool check_and_lock(lobpcg_t* h) {
     if (keep.size() != h->J.size()) {
         // compact the residual block W to the surviving columns
         std::vector<int> nJ;
+        const size_t es = dtype_size(h->tw);
         for (size_t u = 0; u < keep.size(); ++u) {
             if ((int)u != keep[u])
-                LG_CUDA(cudaMemcpyAsync(h->W.p + (int64_t)u * h->ld, h->W.p + (int64_t)keep[u] * h->ld,
-                                        h->g.n() * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+                LG_CUDA(cudaMemcpyAsync(col(h->W, h->tw, h->ld, (int)u), col(h->W, h->tw, h->ld, keep[u]),
+                                        h->g.n() * es, cudaMemcpyDeviceToDevice, h->stream));
             nJ.push_back(h->J[keep[u]]);
         }
         h->J.swap(nJ);
@@ -409,48 +444,57 @@ void pass_body(lobpcg_t* h) {
     const int64_t n = h->g.n();
     const int m = h->m, b = (int)h->J.size();
     const int64_t ld = h->ld;
+    const DType tw = h->tw;
     cudaStream_t st = h->stream;
     PhaseTimer tm(h);
     tm.mark(0);
     // step 9: W_J = T W_J (output in E0, then the buffers swap roles)
-    precond(h, b, h->W.p, ld, h->E0.p, ld, h->T0.p, ld);
+    precond(h, b, tw, h->W.p, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
     tm.mark(1);
     // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
-    const Blocks3 SW = blocks(h->W.p, b, nullptr, 0, nullptr, 0, ld);
+    const Blocks3 SW = blocks(h->W.p, b, tw, nullptr, 0, nullptr, 0, tw, ld);
     gram(h, SW, nullptr, h->gramA, h->Gsmall, nullptr);
     launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
-    launch_apply_rinv(n, b, h->W.p, ld, h->W.p, ld, h->Rinv, h->status,
-                      ST_W_BREAKDOWN, st);
+    launch_apply_rinv(n, b, tw, h->W.p, ld, h->W.p, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
     tm.mark(2);
     // step 12: AW_J = A W_J
-    spmv(h, b, h->W.p, ld, h->AW.p, ld);
+    spmv(h, b, tw, h->W.p, ld, h->AW.p, ld);
     tm.mark(3);
     // steps 13-16: P_J = P_J R^-1, AP_J = AP_J R^-1 with R = chol(P_J^T P_J)
     const bool use_p = h->k > 0;
-    double* Pj = h->P.p;
-    double* APj = h->AP.p;
+    void* Pj = h->P.p;
+    void* APj = h->AP.p;
     if (use_p) {
         if (b != m) {
+            const size_t es = dtype_size(tw);
             for (int t = 0; t < b; ++t) {
-                LG_CUDA(cudaMemcpyAsync(h->Pc.p + (int64_t)t * ld, h->P.p + (int64_t)h->J[t] * ld,
-                                        n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                LG_CUDA(cudaMemcpyAsync(h->APc.p + (int64_t)t * ld, h->AP.p + (int64_t)h->J[t] * ld,
-                                        n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                LG_CUDA(cudaMemcpyAsync(col(h->Pc, tw, ld, t), col(h->P, tw, ld, h->J[t]), n * es,
+                                        cudaMemcpyDeviceToDevice, st));
+                if (h->precision != LOBPCG_MIXED)
+                    LG_CUDA(cudaMemcpyAsync(col(h->APc, tw, ld, t), col(h->AP, tw, ld, h->J[t]), n * es,
+                                            cudaMemcpyDeviceToDevice, st));
             }
             Pj = h->Pc.p;
             APj = h->APc.p;
         }
-        const Blocks3 SP = blocks(Pj, b, nullptr, 0, nullptr, 0, ld);
+        const Blocks3 SP = blocks(Pj, b, tw, nullptr, 0, nullptr, 0, tw, ld);
         gram(h, SP, nullptr, h->gramA, h->Gsmall, nullptr);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
-        launch_apply_rinv(n, b, Pj, ld, Pj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
-        launch_apply_rinv(n, b, APj, ld, APj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+        launch_apply_rinv(n, b, tw, Pj, ld, Pj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+        if (h->precision == LOBPCG_MIXED) {
+            // Mixed form: AP_J = A P_J by one more (float32) SpMV.  P_J is nearly rank deficient
+            // near convergence, and R^-1 would magnify the separate float32 roundings of P_J and
+            // AP_J so much that AP_J R^-1 no longer matches A (P_J R^-1).
+            spmv(h, b, tw, Pj, ld, APj, ld);
+        } else {
+            launch_apply_rinv(n, b, tw, APj, ld, APj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+        }
     }
     tm.mark(4);
     // steps 17-23: Gram matrices of the basis [X W_J P_J]
-    const Blocks3 S = blocks(h->X.p, m, h->W.p, b, Pj, use_p ? b : 0, ld);
-    const Blocks3 AS = blocks(h->AX.p, m, h->AW.p, b, APj, use_p ? b : 0, ld);
+    const Blocks3 S = blocks(h->X.p, m, DT_F64, h->W.p, b, Pj, use_p ? b : 0, tw, ld);
+    const Blocks3 AS = blocks(h->AX.p, m, DT_F64, h->AW.p, b, APj, use_p ? b : 0, tw, ld);
     const int q = S.q();
     gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
     tm.mark(5);
@@ -460,19 +504,18 @@ void pass_body(lobpcg_t* h) {
     tm.mark(6);
     // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
     const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
-    launch_update(n, m, S, h->Cm, h->X.p, h->P.p, ld, h->status, skip, st);
-    launch_update(n, m, AS, h->Cm, h->AX.p, h->AP.p, ld, h->status, skip, st);
+    launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st);
+    launch_update(n, m, AS, h->Cm, f64(h->AX), h->AP.p, ld, h->status, skip, st);
     tm.mark(7);
     // step 7 of the next pass
     residual_into_W(h);
     const unsigned stw = fetch_small(h);
     if (h->phase_timing) {
-        // event 0..7 bracket phases 1..7 of this pass; the residual phase is the tail
+        // events 0..7 bracket phases 1..7 of this pass; the residual phase is the tail
         for (int i = 0; i < 7; ++i) {
             float ms = 0.f;
             LG_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
-            const int ph = i + 1;   // PH_PRECOND .. PH_UPDATE
-            h->phase_ms[ph] += ms;
+            h->phase_ms[i + 1] += ms;
         }
     }
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
@@ -486,14 +529,27 @@ void pass_body(lobpcg_t* h) {
     h->pending_check = true;
 }
 
+// Mixed form, once every implicit residual passed: float64 correction sweep on X.  Afterwards J
+// holds the columns whose float64 residual still fails.
+void fp64_correction(lobpcg_t* h) {
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    orthonormalize_and_rr(h);
+    const unsigned stw = fetch_small(h);
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    check_setup_status(h, stw);
+    ++h->fp64_sweeps;
+    h->pending_check = true;
+}
+
 // Residuals of all m columns from A X (not the implicitly updated AX); host resid.
 void finish(lobpcg_t* h) {
     const int64_t n = h->g.n();
     const int m = h->m;
-    spmv(h, m, h->X.p, h->ld, h->T0.p, h->ld);
+    spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
     ColList cols = identity_cols(m);
-    launch_residual(n, cols, h->X.p, h->T0.p, h->ld, h->lam, nullptr, 0, h->part.p, h->stream);
-    launch_norms_finalize(m, residual_chunks(n), h->part.p, h->norms, h->stream);
+    launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, DT_F64, nullptr, 0, f64(h->part),
+                    h->stream);
+    launch_norms_finalize(m, residual_chunks(n), f64(h->part), h->norms, h->stream);
     h->resid_h.resize(m);
     LG_CUDA(cudaMemcpyAsync(h->resid_h.data(), h->norms, m * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
@@ -511,24 +567,31 @@ void fill_info(lobpcg_t* h, lobpcg_info* out, int status) {
     out->iters = h->k;
     out->active = (int)h->J.size();
     out->p_dropped = h->p_dropped;
+    out->fp64_sweeps = h->fp64_sweeps;
     double mr = 0.0;
     for (int j = 0; j < (int)h->resid_h.size() && j < (int)h->lam_h.size(); ++j)
         mr = std::max(mr, h->resid_h[j] / std::fabs(h->lam_h[j]));
     out->max_rel_resid = mr;
     out->setup_ms = h->setup_ms;
-    out->kernel_launches = g_kernel_launches.load() - h->launches_at_start;
     out->solve_ms = h->solve_ms;
+    out->kernel_launches = g_kernel_launches.load() - h->launches_at_start;
     for (int i = 0; i < LOBPCG_NPHASES; ++i) out->phase_ms[i] = h->phase_ms[i];
 }
 
-// Passes until J is empty or `steps` passes ran.  Returns OK / NOT_CONVERGED.
-int run_passes(lobpcg_t* h, int steps, bool last_is_check_only) {
+// Passes until J is empty (in the mixed form: confirmed by the float64 correction sweep) or
+// `steps` passes ran.  Returns OK / NOT_CONVERGED.
+int run_passes(lobpcg_t* h, int steps) {
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES], h->stream));
     int rc = LOBPCG_NOT_CONVERGED;
     for (int s = 0; s <= steps; ++s) {
-        if (check_and_lock(h)) { rc = LOBPCG_OK; break; }
+        bool empty = check_and_lock(h);
+        if (empty && h->precision == LOBPCG_MIXED) {
+            if (h->fp64_sweeps >= kMaxFp64Sweeps) break;   // not confirmed: NOT_CONVERGED
+            fp64_correction(h);
+            empty = check_and_lock(h);
+        }
+        if (empty) { rc = LOBPCG_OK; break; }
         if (s == steps) break;
-        (void)last_is_check_only;
         pass_body(h);
     }
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], h->stream));
@@ -564,7 +627,6 @@ int guarded(lobpcg_t* h, F&& f) {
 bool valid_ld(int64_t ld, int64_t n) { return ld >= n; }
 
 }  // namespace
-
 // ====================================================================== C ABI
 extern "C" {
 
@@ -572,8 +634,8 @@ int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocat
                   int precision) {
     if (!out) return LOBPCG_ERR_ARG;
     *out = nullptr;
-    if (precision != LOBPCG_FP64) {
-        g_handle_free_error = "only LOBPCG_FP64 is available";
+    if (precision != LOBPCG_FP64 && precision != LOBPCG_MIXED) {
+        g_handle_free_error = "precision must be LOBPCG_FP64 or LOBPCG_MIXED";
         return LOBPCG_ERR_ARG;
     }
     int ndev = 0;
@@ -591,6 +653,8 @@ int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocat
     h->device = device;
     h->stream = (cudaStream_t)stream;
     h->precision = precision;
+    h->tw = precision == LOBPCG_MIXED ? DT_F32 : DT_F64;
+    h->tl = precision == LOBPCG_MIXED ? DT_BF16 : DT_F64;
     if (alloc) {
         h->alloc = *alloc;
         h->has_alloc = true;
@@ -664,7 +728,7 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre, int
         h->nu_post = nu_post;
         h->omega = omega;
         ensure(h, h->coarse_tab, coarse_tables_size(lv.back()) * sizeof(double));
-        launch_coarse_setup(lv.back(), ls.back(), h->coarse_tab.p, h->stream);
+        launch_coarse_setup(lv.back(), ls.back(), f64(h->coarse_tab), h->stream);
         h->pc_kind = LOBPCG_PRECOND_GMG;
         h->state = 0;
         return LOBPCG_OK;
@@ -717,7 +781,7 @@ int lobpcg_iterate(lobpcg_t* h, int steps, lobpcg_info* out) {
         LG_REQUIRE(steps >= 0, LOBPCG_ERR_ARG, "steps must be >= 0");
         int r = LOBPCG_NOT_CONVERGED;
         // `steps` passes of steps 7-33, then the check of the pass after them
-        r = run_passes(h, steps, false);
+        r = run_passes(h, steps);
         return r;
     });
     if (h && out) fill_info(h, out, rc);
@@ -742,7 +806,7 @@ int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed, lobpc
         begin(h, m, tol, seed);
         int r = LOBPCG_NOT_CONVERGED;
         try {
-            r = run_passes(h, maxit, true);
+            r = run_passes(h, maxit);
         } catch (const Error& e) {
             if (e.code == LOBPCG_ERR_CUDA) throw;
             finish(h);   // last valid iterate stays available
@@ -752,7 +816,6 @@ int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed, lobpc
         return r;
     });
     if (h && out) fill_info(h, out, rc);
-    if (h) h->last_status = rc;
     return rc;
 }
 
@@ -814,7 +877,7 @@ int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx, doub
         const int64_t n = h->g.n();
         LG_REQUIRE(X && Y && ncols >= 0 && valid_ld(ldx, n) && valid_ld(ldy, n), LOBPCG_ERR_ARG,
                    "invalid stencil arguments");
-        spmv(h, ncols, X, ldx, Y, ldy);
+        spmv(h, ncols, DT_F64, X, ldx, Y, ldy);
         LG_CUDA(cudaStreamSynchronize(h->stream));
         return LOBPCG_OK;
     });
@@ -827,8 +890,10 @@ int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr, doub
         LG_REQUIRE(R && E && ncols >= 1 && ncols <= LOBPCG_MAX_M && valid_ld(ldr, n) &&
                        valid_ld(lde, n),
                    LOBPCG_ERR_ARG, "invalid preconditioner arguments");
+        LG_REQUIRE(h->precision == LOBPCG_FP64, LOBPCG_ERR_ARG,
+                   "lobpcg_op_precond needs a LOBPCG_FP64 handle");
         ensure_workspace(h, std::max(h->wm, ncols));
-        precond(h, ncols, R, ldr, E, lde, h->T0.p, h->ld);
+        precond(h, ncols, DT_F64, R, ldr, E, lde, h->T0.p, h->ld);
         LG_CUDA(cudaStreamSynchronize(h->stream));
         return LOBPCG_OK;
     });
@@ -846,8 +911,8 @@ int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X,
         ColList cl{};
         cl.n = ncols;
         for (int t = 0; t < ncols; ++t) cl.idx[t] = cols[t];
-        launch_residual(n, cl, X, AX, ld, lambda, W, ldw, h->part.p, h->stream);
-        launch_norms_finalize(ncols, residual_chunks(n), h->part.p, h->norms, h->stream);
+        launch_residual(n, cl, X, AX, ld, lambda, DT_F64, W, ldw, f64(h->part), h->stream);
+        launch_norms_finalize(ncols, residual_chunks(n), f64(h->part), h->norms, h->stream);
         LG_CUDA(cudaMemcpyAsync(norms, h->norms, ncols * sizeof(double), cudaMemcpyDeviceToHost,
                                 h->stream));
         LG_CUDA(cudaStreamSynchronize(h->stream));
@@ -868,8 +933,8 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
         LG_REQUIRE(!AS0 || (gramA && (w1 == 0 || AS1) && (w2 == 0 || AS2)), LOBPCG_ERR_ARG,
                    "invalid Gram arguments (A side)");
         ensure_workspace(h, std::max(h->wm, (q + 2) / 3));
-        const Blocks3 S = blocks(S0, w0, S1, w1, S2, w2, ld);
-        const Blocks3 AS = blocks(AS0, w0, AS1, w1, AS2, w2, ld);
+        const Blocks3 S = blocks(S0, w0, DT_F64, S1, w1, S2, w2, DT_F64, ld);
+        const Blocks3 AS = blocks(AS0, w0, DT_F64, AS1, w1, AS2, w2, DT_F64, ld);
         gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr);
         LG_CUDA(cudaStreamSynchronize(h->stream));
         return LOBPCG_OK;
@@ -885,11 +950,11 @@ int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld) {
         ensure_workspace(h, std::max(h->wm, b));
         cudaStream_t st = h->stream;
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
-        const Blocks3 SV = blocks(V, b, nullptr, 0, nullptr, 0, ld);
+        const Blocks3 SV = blocks(V, b, DT_F64, nullptr, 0, nullptr, 0, DT_F64, ld);
         gram(h, SV, nullptr, h->gramA, h->Gsmall, nullptr);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
-        launch_apply_rinv(n, b, V, ld, V, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
-        if (AV) launch_apply_rinv(n, b, AV, ld, AV, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        launch_apply_rinv(n, b, DT_F64, V, ld, V, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        if (AV) launch_apply_rinv(n, b, DT_F64, AV, ld, AV, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
         unsigned stw = 0;
         LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         LG_CUDA(cudaStreamSynchronize(st));

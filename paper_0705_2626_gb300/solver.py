@@ -58,7 +58,10 @@ class Solver:
 
     def __init__(self, dims, scale=None, precond="gmg", levels=None, nu=2, omega=2.0 / 3.0,
                  device=0, stream=None, tol_mode="relative", gram="explicit", phase_timing=False,
-                 torch_allocator=True):
+                 torch_allocator=True, precision="fp64"):
+        if precision not in ("fp64", "mixed"):
+            raise ValueError(f"precision must be 'fp64' or 'mixed', not {precision!r}")
+        self.precision = precision
         self.dims = tuple(int(d) for d in dims)
         self.n = self.dims[0] * self.dims[1] * self.dims[2]
         self.scale = default_scale(self.dims) if scale is None else float(scale)
@@ -67,7 +70,8 @@ class Solver:
         self._alloc = _TorchAllocator(device) if torch_allocator else None
         h = ctypes.c_void_p()
         _check(capi.lobpcg_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
-                                  ctypes.byref(self._alloc.struct) if self._alloc else None, capi.FP64))
+                                  ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                  capi.MIXED if precision == "mixed" else capi.FP64))
         self.h = h
         _check(capi.lobpcg_set_operator(h, capi.LAPLACE7, *self.dims, self.scale, None), h)
         if precond == "gmg":
@@ -153,6 +157,7 @@ class Solver:
             _check(capi.lobpcg_get_eigenpairs(self.h, lam, None, self.n, 0, res), self.h)
         return dict(lam=list(lam), resid=list(res), X=X, iters=self.info.iters, status=self.info.status,
                     status_name=capi.STATUS_NAMES.get(self.info.status), active=self.info.active,
-                    p_dropped=self.info.p_dropped, setup_ms=self.info.setup_ms, solve_ms=self.info.solve_ms,
+                    p_dropped=self.info.p_dropped, fp64_sweeps=self.info.fp64_sweeps,
+                    setup_ms=self.info.setup_ms, solve_ms=self.info.solve_ms,
                     max_rel_resid=self.info.max_rel_resid, kernel_launches=self.info.kernel_launches,
                     phase_ms=dict(zip(capi.PHASE_NAMES, list(self.info.phase_ms))))
