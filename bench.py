@@ -162,7 +162,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     seed = 2 + rank
-    s = Solver(dims, levels=levels, device=local_rank)
+    s = Solver(dims, levels=levels, device=local_rank, precision=args.precision)
     stream = s.stream
 
     def barrier():
@@ -210,7 +210,16 @@ def run_ours(args, rank, world, local_rank):
     # ---- time to tolerance (tol 1e-8), device time of the iteration loop
     out = s.solve(m, tol=1e-8, maxit=200, seed=seed)
     ttt = dict(time_to_tol_s=(out["solve_ms"]) / 1e3, setup_s=out["setup_ms"] / 1e3, iters=out["iters"],
-               status=out["status_name"], max_rel_resid=out["max_rel_resid"], tol=1e-8)
+               status=out["status_name"], max_rel_resid=out["max_rel_resid"], tol=1e-8,
+               fp64_sweeps=out["fp64_sweeps"], lam=out["lam"])
+    other = "mixed" if args.precision == "fp64" else "fp64"
+    so = Solver(dims, levels=levels, device=local_rank, precision=other)
+    oo = so.solve(m, tol=1e-8, maxit=200, seed=seed)
+    so.close()
+    lam_diff = max(abs(a - b) / abs(b) for a, b in zip(oo["lam"], out["lam"]))
+    ttt_other = dict(precision=other, time_to_tol_s=oo["solve_ms"] / 1e3, iters=oo["iters"], status=oo["status_name"],
+                     max_rel_resid=oo["max_rel_resid"], fp64_sweeps=oo["fp64_sweeps"],
+                     max_rel_lambda_diff_vs_timed_form=lam_diff)
 
     # ---- end to end through the public API with host buffers: X0 from pinned host memory in,
     # eigenvalues and eigenvectors back to pinned host memory, K iterations (tol 0)
@@ -245,12 +254,13 @@ def run_ours(args, rank, world, local_rank):
                           "(numpy elementwise single-threaded, BLAS multi-threaded)")
     line = dict(
         metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f64" if args.precision == "fp64" else "f64+f32+bf16",
         data="synthetic",
         config=dict(workload=workload_desc(w), grid=list(dims), m=m, levels=levels, tol_timed=0.0,
                     l2="no flush: the 6 stored blocks are 1.6 GB, far above the 129 MB L2",
                     parallelism="replicas" if world > 1 else "single-gpu"),
-        time_to_tol=ttt, phase_ms_per_iter=phase,
+        precision=args.precision, time_to_tol=ttt, time_to_tol_other_form=ttt_other, phase_ms_per_iter=phase,
         roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles)", bound="alu",
                       achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=achieved / FP64_PEAK_TFLOPS,
                       traffic=traffic, peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
@@ -266,6 +276,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="form of the timed steps; the other form's time to tolerance is reported beside it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -123,6 +123,9 @@ int gram_parts(int64_t n);
 int64_t gram_scratch_doubles(int64_t n, int q);
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st);
+// S^T S partials in plain float32 products (block 0 may be float64, converted on load): the
+// projection coefficients of the mixed form, where float32 accuracy suffices.
+void launch_gram_f32(int64_t n, const Blocks3& S, double* part, int nparts, cudaStream_t st);
 // gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
 // summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
 // diagonal blocks of gramB are identities (steps 18-22 as printed).
@@ -142,6 +145,11 @@ void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void*
 void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout,
                    void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
                    cudaStream_t st);
+
+// Mixed form, block Gram-Schmidt: V -= S0 C[0:w0, :] + S1 C[w0:w0+w1, :] (V and S1 float32,
+// S0 float64, C float64 with leading dimension ldc), float32 arithmetic.
+void launch_project(int64_t n, int b, float* V, const double* S0, int w0, const float* S1, int w1,
+                    int64_t ld, const double* C, int ldc, cudaStream_t st);
 
 // ---------------------------------------------------------------- small dense
 // Rinv = R^-1, R = chol(G) on the unit-diagonal scaling of G (b x b).  On failure sets

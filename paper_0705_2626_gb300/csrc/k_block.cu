@@ -96,6 +96,7 @@ __global__ void k_norms_finalize(int nchunks, const double* __restrict__ partial
 
 // ------------------------------------------------------------------ Gram
 constexpr int kTM = 4;    // each thread owns a kTM x kTM tile of the output
+constexpr int kCG = 4;    // output columns per thread of the update-type kernels
 
 template <typename T0, typename T12, typename C>
 __device__ __forceinline__ C load_col(const Blocks3& B, int c, int64_t p) {
@@ -270,6 +271,232 @@ __global__ void __launch_bounds__(kGramMaxThreads)
         }
 }
 
+// Mixed-form Gram: block 0 (X, AX) float64, blocks 1-2 (W, P families) float32.  Tiles in the
+// X rows of the output (the blocks X^T AX, X^T AW, X^T AP, X^T X, X^T W, X^T P) are computed in
+// double-float arithmetic: every float64 entry is split into float32 hi + lo parts when it is
+// staged in shared memory, hi * hi products are made exact with an FMA, the hi * lo cross terms
+// are added, and the sums are kept as unevaluated float32 pairs (two-sum), about 2^-44 relative.
+// These blocks couple the float64 Ritz vectors with the float32 search directions; their
+// float32 roundings would otherwise not cancel (A W has large terms while X^T A W is small) and
+// would limit the attainable residual.  The remaining tiles (W and P only) use float32 products
+// summed per stage with Kahan compensation across stages.  Tiles are ordered double-float first.
+struct MixedTile {
+    int ti, tj;
+    bool isA, df;
+};
+
+__device__ MixedTile mixed_tile(const Blocks3& S, int q, int with_a, int idx) {
+    const int T = (q + kTM - 1) / kTM;
+    const int xrows = (S.w[0] + kTM - 1) / kTM;     // tile rows that touch X
+    MixedTile r{0, 0, false, false};
+    int u = idx;
+    for (int pass = 0; pass < 2; ++pass) {           // pass 0: double-float tiles, 1: float32
+        const bool df = pass == 0;
+        if (with_a)
+            for (int ti = 0; ti < T; ++ti) {
+                if ((ti < xrows) != df) continue;
+                for (int tj = 0; tj < T; ++tj)
+                    if (a_tile_needed(S, q, ti, tj)) {
+                        if (u == 0) return MixedTile{ti, tj, true, df};
+                        --u;
+                    }
+            }
+        for (int ti = 0; ti < T; ++ti) {
+            if ((ti < xrows) != df) continue;
+            for (int tj = ti; tj < T; ++tj) {
+                if (u == 0) return MixedTile{ti, tj, false, df};
+                --u;
+            }
+        }
+    }
+    return r;
+}
+
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+__global__ void __launch_bounds__(kGramMaxThreads)
+    k_gram_mixed(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
+                 double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float* sm = reinterpret_cast<float*>(sm_raw);
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    const GramShape gs = gram_shape(S, with_a != 0, 16);   // 4 float planes per staged value
+    const int nt = gs.ntA + gs.ntB;
+    const int ldsm = T * kTM + 1;
+    const int plane = gs.gk * ldsm;
+    float* sSh = sm;
+    float* sSl = sm + plane;
+    float* sAh = sm + 2 * plane;
+    float* sAl = sm + 3 * plane;
+    const int tile = threadIdx.x % nt;
+    const int grp = threadIdx.x / nt;
+    const bool active = grp < gs.ks;
+    const MixedTile mt = mixed_tile(S, q, with_a, tile);
+    const int ti = mt.ti, tj = mt.tj;
+    const int w0 = S.w[0];
+
+    // double-float tiles: tot = hi, cmp = lo of the running sums; float32 tiles: st_ = the stage's
+    // sums, tot / cmp = Kahan sum and compensation
+    float st_[kTM][kTM], tot[kTM][kTM], cmp[kTM][kTM];
+#pragma unroll
+    for (int a = 0; a < kTM; ++a)
+#pragma unroll
+        for (int b = 0; b < kTM; ++b) st_[a][b] = tot[a][b] = cmp[a][b] = 0.f;
+
+    const int64_t r0 = blockIdx.x * rows_per_part;
+    const int64_t r1 = min(n, r0 + rows_per_part);
+    const float* rh = mt.isA ? sAh : sSh;
+    const float* rl = mt.isA ? sAl : sSl;
+    for (int64_t base = r0; base < r1; base += gs.gk) {
+        for (int e = threadIdx.x; e < gs.gk * T * kTM; e += blockDim.x) {
+            const int c = e / gs.gk, k = e - c * gs.gk;
+            const int64_t p = base + k;
+            float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
+            if (c < q && p < r1) {
+                if (c < w0) {
+                    split_f64(__ldg(static_cast<const double*>(S.p[0]) + (int64_t)c * S.ld + p), sh, sl);
+                    if (with_a) split_f64(__ldg(static_cast<const double*>(AS.p[0]) + (int64_t)c * AS.ld + p), ah, al);
+                } else {
+                    sh = load_col<double, float, float>(S, c, p);
+                    if (with_a) ah = load_col<double, float, float>(AS, c, p);
+                }
+            }
+            sSh[k * ldsm + c] = sh;
+            sSl[k * ldsm + c] = sl;
+            if (with_a) { sAh[k * ldsm + c] = ah; sAl[k * ldsm + c] = al; }
+        }
+        __syncthreads();
+        if (active) {
+            if (mt.df) {
+                for (int k = grp; k < gs.gk; k += gs.ks) {
+                    float xh[kTM], xl[kTM], yh[kTM], yl[kTM];
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u) {
+                        xh[u] = sSh[k * ldsm + ti * kTM + u];
+                        xl[u] = sSl[k * ldsm + ti * kTM + u];
+                        yh[u] = rh[k * ldsm + tj * kTM + u];
+                        yl[u] = rl[k * ldsm + tj * kTM + u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                        for (int v = 0; v < kTM; ++v) {
+                            const float p = xh[u] * yh[v];
+                            float err = fmaf(xh[u], yh[v], -p);
+                            err = fmaf(xh[u], yl[v], err);
+                            err = fmaf(xl[u], yh[v], err);
+                            const float t = tot[u][v] + p;          // two-sum of (hi, p)
+                            const float z = t - tot[u][v];
+                            const float d = (tot[u][v] - (t - z)) + (p - z);
+                            tot[u][v] = t;
+                            cmp[u][v] += d + err;
+                        }
+                }
+            } else {
+                for (int k = grp; k < gs.gk; k += gs.ks) {
+                    float a[kTM], b[kTM];
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u) {
+                        a[u] = sSh[k * ldsm + ti * kTM + u];
+                        b[u] = rh[k * ldsm + tj * kTM + u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                        for (int v = 0; v < kTM; ++v) st_[u][v] = fmaf(a[u], b[v], st_[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                    for (int v = 0; v < kTM; ++v) {
+                        const float y = st_[u][v] - cmp[u][v];
+                        const float t = tot[u][v] + y;
+                        cmp[u][v] = (t - tot[u][v]) - y;
+                        tot[u][v] = t;
+                        st_[u][v] = 0.f;
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    double res[kTM][kTM];
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v)
+            res[u][v] = mt.df ? (double)tot[u][v] + (double)cmp[u][v] : (double)tot[u][v] - (double)cmp[u][v];
+    if (gs.ks > 1) {
+        double* red = reinterpret_cast<double*>(sm_raw);   // [ks][nt][16]
+        if (active)
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) {
+                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
+                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
+                    res[u][v] = sum;
+                }
+        }
+    }
+    if (grp != 0) return;
+    double* out = part + (int64_t)blockIdx.x * 2 * q * q + (mt.isA ? 0 : (int64_t)q * q);
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v) {
+            const int i = ti * kTM + u, j = tj * kTM + v;
+            if (i < q && j < q) out[i + (int64_t)q * j] = res[u][v];
+        }
+}
+
+// Block Gram-Schmidt step of the mixed form: V -= S0 C0 + S1 C1 for the b columns of V (float32),
+// S0 float64 (w0 columns: X), S1 float32 (w1 columns: W, or none), C (w0 + w1) x b column-major
+// float64.  Float32 arithmetic; each thread owns one grid point and kCG columns of V.
+__global__ void k_project(int64_t n, int b, float* V, const double* __restrict__ S0, int w0,
+                          const float* __restrict__ S1, int w1, int64_t ld,
+                          const double* __restrict__ C, int ldc) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float* sC = reinterpret_cast<float*>(sm_raw);        // (w0 + w1) x b
+    const int r = w0 + w1;
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < r * b; e += 32 * blockDim.y)
+        sC[e] = (float)C[(e % r) + (int64_t)ldc * (e / r)];
+    __syncthreads();
+    const int c0 = threadIdx.y * kCG;
+    for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
+        const int64_t p = base + threadIdx.x;
+        if (p >= n) continue;
+        float acc[kCG];
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) acc[c] = 0.f;
+        for (int i = 0; i < w0; ++i) {
+            const float v = (float)__ldg(S0 + (int64_t)i * ld + p);
+#pragma unroll
+            for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[i + r * min(c0 + c, b - 1)], acc[c]);
+        }
+        for (int i = 0; i < w1; ++i) {
+            const float v = __ldg(S1 + (int64_t)i * ld + p);
+#pragma unroll
+            for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[w0 + i + r * min(c0 + c, b - 1)], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kCG; ++c)
+            if (c0 + c < b) {
+                float* vp = V + (int64_t)(c0 + c) * ld + p;
+                *vp = *vp - acc[c];
+            }
+    }
+}
+
 // One warp per unordered pair (i <= j): fixed-order sums of the partials.  gramA(i, j) is the
 // symmetrised sum inside a diagonal block and the upper-block entry S_i^T AS_j otherwise.
 __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ part, int with_a,
@@ -310,7 +537,6 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
 }
 
 // ------------------------------------------------------------------ Ritz update
-constexpr int kCG = 4;   // output columns per thread
 
 // Pout = S1 C1 + S2 C2 (arithmetic CW, stored TW) and Xout = S0 C0 + Pout (float64).
 // S0 is float64; S1, S2 have type TW.  Each thread owns one grid point and kCG output columns.
@@ -468,14 +694,37 @@ static void gram_t(int64_t n, const Blocks3& S, const Blocks3* AS, double* part,
     k_gram<T0, T12, C><<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
 }
 
+static void gram_mixed(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
+                       cudaStream_t st) {
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    const GramShape gs = gram_shape(S, AS != nullptr, 16);
+    const int nt = gs.ntA + gs.ntB;
+    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
+    LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
+    const size_t stage = 4 * (size_t)gs.gk * (T * kTM + 1) * sizeof(float);
+    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
+    const size_t smem = std::max(stage, red);
+    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
+    const int64_t rows = ceil_div(n, nparts);
+    Blocks3 A = AS ? *AS : S;
+    k_gram_mixed<<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
+}
+
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st) {
     const bool has12 = S.w[1] + S.w[2] > 0;
     const DType t12 = has12 ? S.t12 : S.t0;
     if (S.t0 == DT_F64 && t12 == DT_F64) gram_t<double, double, double>(n, S, AS, part, nparts, st);
-    else if (S.t0 == DT_F64 && t12 == DT_F32) gram_t<double, float, float>(n, S, AS, part, nparts, st);
+    else if (S.t0 == DT_F64 && t12 == DT_F32) gram_mixed(n, S, AS, part, nparts, st);
     else if (S.t0 == DT_F32 && t12 == DT_F32) gram_t<float, float, float>(n, S, AS, part, nparts, st);
     else throw Error(LOBPCG_ERR_ARG, "unsupported Gram block types");
+    LG_CHECK_LAUNCH();
+}
+
+void launch_gram_f32(int64_t n, const Blocks3& S, double* part, int nparts, cudaStream_t st) {
+    if (S.t0 == DT_F64) gram_t<double, float, float>(n, S, nullptr, part, nparts, st);
+    else gram_t<float, float, float>(n, S, nullptr, part, nparts, st);
     LG_CHECK_LAUNCH();
 }
 
@@ -524,4 +773,16 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
     LG_CHECK_LAUNCH();
 }
 
+}  // namespace lg
+
+namespace lg {
+void launch_project(int64_t n, int b, float* V, const double* S0, int w0, const float* S1, int w1,
+                    int64_t ld, const double* C, int ldc, cudaStream_t st) {
+    if (b <= 0) return;
+    const int groups = (int)ceil_div(b, kCG);
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
+    const size_t smem = (size_t)(w0 + w1) * b * sizeof(float);
+    k_project<<<(unsigned)blocks, dim3(32, groups), smem, st>>>(n, b, V, S0, w0, S1, w1, ld, C, ldc);
+    LG_CHECK_LAUNCH();
+}
 }  // namespace lg

@@ -50,12 +50,25 @@ __global__ void __launch_bounds__(kTX* kTY)
     const bool hasl = i > 0, hasr = i + 1 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
     for (int k = k0; k < k1; ++k, p += sz) {
         const C xp = (k + 1 < g.nz) ? ld_as(xc + p + sz) : C(0);
-        C nb = xm + xp;
-        if (hasl) nb += ld_as(xc + p - 1);
-        if (hasr) nb += ld_as(xc + p + 1);
-        if (hasd) nb += ld_as(xc + p - sy);
-        if (hasu) nb += ld_as(xc + p + sy);
-        C v = fma(b, nb, a * x0);
+        C v;
+        if constexpr (sizeof(C) == 8) {
+            C nb = xm + xp;
+            if (hasl) nb += ld_as(xc + p - 1);
+            if (hasr) nb += ld_as(xc + p + 1);
+            if (hasd) nb += ld_as(xc + p - sy);
+            if (hasu) nb += ld_as(xc + p + sy);
+            v = fma(b, nb, a * x0);
+        } else {
+            // float32 arithmetic: y = (a + 6b) x - b * sum_q (x - x_q).  For a smooth field the
+            // neighbour differences are exact (Sterbenz), so A x = s sum (x - x_q) keeps its
+            // relative accuracy instead of losing it to the cancellation in 6x - sum x_q.
+            C d = (x0 - xm) + (x0 - xp);
+            d += hasl ? x0 - ld_as(xc + p - 1) : x0;
+            d += hasr ? x0 - ld_as(xc + p + 1) : x0;
+            d += hasd ? x0 - ld_as(xc + p - sy) : x0;
+            d += hasu ? x0 - ld_as(xc + p + sy) : x0;
+            v = fma(-b, d, (a + C(6) * b) * x0);
+        }
         if (HAS_Z) v = fma(c, ld_as(zc + p), v);
         st_as(yc + p, v);
         xm = x0;

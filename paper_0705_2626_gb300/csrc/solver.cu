@@ -303,6 +303,27 @@ void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* 
     launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
 }
 
+// Mixed form: two passes of block Gram-Schmidt of V (b float32 columns) against X (m float64
+// columns) and, if W != null, against W (b float32 columns).  The trial subspace of the
+// Rayleigh-Ritz step is unchanged; the basis [X W P] becomes well conditioned, which the
+// float32 search directions need (with near-dependent columns the float32 roundings of the Gram
+// matrices would be magnified into spurious Ritz pairs).
+void project_out(lobpcg_t* h, int b, void* V, const void* W) {
+    const int64_t n = h->g.n();
+    const int m = h->m;
+    const int wb = W ? b : 0;
+    const int q = m + wb + b;
+    const int nparts = gram_parts(n);
+    for (int pass = 0; pass < 2; ++pass) {
+        const Blocks3 S = blocks(h->X.p, m, DT_F64, W ? W : V, W ? b : b, V, W ? b : 0, DT_F32, h->ld);
+        launch_gram_f32(n, S, f64(h->part), nparts, h->stream);
+        launch_gram_finalize(q, nparts, f64(h->part), false, nullptr, h->gramB, nullptr, &S, h->stream);
+        // coefficients: rows 0 .. m + wb - 1 of the last b columns of gramB
+        launch_project(n, b, static_cast<float*>(V), f64(h->X), m, static_cast<const float*>(W), wb, h->ld,
+                       h->gramB + (size_t)(m + wb) * q, q, h->stream);
+    }
+}
+
 // ------------------------------------------------------------------ timing
 struct PhaseTimer {
     lobpcg_t* h;
@@ -451,6 +472,8 @@ void pass_body(lobpcg_t* h) {
     // step 9: W_J = T W_J (output in E0, then the buffers swap roles)
     precond(h, b, tw, h->W.p, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
+    const bool mixed = h->precision == LOBPCG_MIXED;
+    if (mixed) project_out(h, b, h->W.p, nullptr);
     tm.mark(1);
     // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
     const Blocks3 SW = blocks(h->W.p, b, tw, nullptr, 0, nullptr, 0, tw, ld);
@@ -478,6 +501,7 @@ void pass_body(lobpcg_t* h) {
             Pj = h->Pc.p;
             APj = h->APc.p;
         }
+        if (mixed) project_out(h, b, Pj, h->W.p);
         const Blocks3 SP = blocks(Pj, b, tw, nullptr, 0, nullptr, 0, tw, ld);
         gram(h, SP, nullptr, h->gramA, h->Gsmall, nullptr);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
@@ -505,7 +529,14 @@ void pass_body(lobpcg_t* h) {
     // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
     const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
     launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st);
-    launch_update(n, m, AS, h->Cm, f64(h->AX), h->AP.p, ld, h->status, skip, st);
+    if (mixed) {
+        // Mixed form: AX = A X by a float64 SpMV (cheaper than the float64 update AX C_X, and
+        // free of the drift that float32 AP would add to an implicitly updated AX).  AP is
+        // recomputed from P in the next pass.
+        spmv(h, m, DT_F64, h->X.p, ld, h->AX.p, ld);
+    } else {
+        launch_update(n, m, AS, h->Cm, f64(h->AX), h->AP.p, ld, h->status, skip, st);
+    }
     tm.mark(7);
     // step 7 of the next pass
     residual_into_W(h);
