@@ -142,14 +142,19 @@ void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void*
 // Xout = S0 C0 + Pout (float64), with C (q x m, column-major, ld q, float64) split by rows into
 // C0 (w0), C1 (w1), C2 (w2).  Xout may alias S0 and Pout may alias S2; Pout may be null.
 // Skipped if *status & skip_mask.
+// If Xh is non-null, also writes the float32 hi / lo planes of Xout (mixed form).
 void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout,
                    void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
-                   cudaStream_t st);
+                   cudaStream_t st, float* Xh = nullptr, float* Xl = nullptr);
 
-// Mixed form, block Gram-Schmidt: V -= S0 C[0:w0, :] + S1 C[w0:w0+w1, :] (V and S1 float32,
-// S0 float64, C float64 with leading dimension ldc), float32 arithmetic.
-void launch_project(int64_t n, int b, float* V, const double* S0, int w0, const float* S1, int w1,
+// Mixed form, block Gram-Schmidt: V -= S0 C[0:w0, :] + S1 C[w0:w0+w1, :] (V, S0 = the float32
+// plane of X, S1 float32; C float64 with leading dimension ldc), float32 arithmetic.
+void launch_project(int64_t n, int b, float* V, const float* S0, int w0, const float* S1, int w1,
                     int64_t ld, const double* C, int ldc, cudaStream_t st);
+// Mixed-form Gram in residual form (S = [X W P] with X as float32 hi plane S.p[0] and lo plane
+// Xl, T = [R AW AP], R = AX - X Lambda): writes gramA and gramB (q x q) using lam = Lambda.
+void launch_gram_mx(int64_t n, const Blocks3& S, const Blocks3& T, const float* Xl, double* part,
+                    int nparts, const double* lam, double* gramA, double* gramB, cudaStream_t st);
 
 // ---------------------------------------------------------------- small dense
 // Rinv = R^-1, R = chol(G) on the unit-diagonal scaling of G (b x b).  On failure sets

@@ -460,9 +460,9 @@ __global__ void __launch_bounds__(kGramMaxThreads)
 }
 
 // Block Gram-Schmidt step of the mixed form: V -= S0 C0 + S1 C1 for the b columns of V (float32),
-// S0 float64 (w0 columns: X), S1 float32 (w1 columns: W, or none), C (w0 + w1) x b column-major
-// float64.  Float32 arithmetic; each thread owns one grid point and kCG columns of V.
-__global__ void k_project(int64_t n, int b, float* V, const double* __restrict__ S0, int w0,
+// S0 = float32 plane of X (w0 columns), S1 float32 (w1 columns: W, or none), C (w0 + w1) x b
+// column-major float64.  Float32 arithmetic; each thread owns one grid point and kCG columns of V.
+__global__ void k_project(int64_t n, int b, float* V, const float* __restrict__ S0, int w0,
                           const float* __restrict__ S1, int w1, int64_t ld,
                           const double* __restrict__ C, int ldc) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -479,7 +479,7 @@ __global__ void k_project(int64_t n, int b, float* V, const double* __restrict__
 #pragma unroll
         for (int c = 0; c < kCG; ++c) acc[c] = 0.f;
         for (int i = 0; i < w0; ++i) {
-            const float v = (float)__ldg(S0 + (int64_t)i * ld + p);
+            const float v = __ldg(S0 + (int64_t)i * ld + p);
 #pragma unroll
             for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[i + r * min(c0 + c, b - 1)], acc[c]);
         }
@@ -495,6 +495,242 @@ __global__ void k_project(int64_t n, int b, float* V, const double* __restrict__
                 *vp = *vp - acc[c];
             }
     }
+}
+
+// Mixed-form Gram in residual form.  Basis S = [X W P] (X as float32 hi / lo planes, W and P
+// float32) and T = [R AW AP] with R = AX - X Lambda (float32; small near convergence).  Partial
+// sums of
+//   S^T T  at (i, j) for every row i of an X column j (X^T R, W^T R, P^T R) and for the upper
+//          block triangle of the W / P part (W^T AW, W^T AP, P^T AP);
+//   S^T S  upper triangle, the X^T X block in double-float arithmetic (hi * hi exact by FMA,
+//          hi * lo cross terms, two-sum accumulation), the rest in float32.
+// The finalize step forms gramA from them with (AX)^T S_j = Lambda X^T S_j + R^T S_j and
+// X^T AX = (X^T X) Lambda + X^T R, so no float32 product ever has to cancel a large term.
+// Float32 sums are compensated (Kahan) across stages of 16 rows per thread.
+struct MxTile {
+    int ti, tj;
+    bool isA, df;
+};
+
+__host__ __device__ inline bool mx_a_needed(const Blocks3& S, int q, int ti, int tj) {
+    const int cmin = block_of(S, tj * kTM), cmax = block_of(S, min(tj * kTM + kTM - 1, q - 1));
+    const int rmin = block_of(S, ti * kTM), rmax = block_of(S, min(ti * kTM + kTM - 1, q - 1));
+    return cmin == 0 || (rmax >= 1 && rmin <= cmax);
+}
+
+__host__ __device__ inline GramShape mx_shape(const Blocks3& S) {
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    GramShape g;
+    g.ntA = 0;
+    for (int ti = 0; ti < T; ++ti)
+        for (int tj = 0; tj < T; ++tj) g.ntA += mx_a_needed(S, q, ti, tj);
+    g.ntB = T * (T + 1) / 2;
+    const int nt = g.ntA + g.ntB;
+    g.ks = max(1, min(8, 256 / nt));
+    while (g.ks > 1 && max(3 * 16 * g.ks * (T * kTM + 1) * 4, g.ks * nt * 16 * 8) > 48 * 1024) --g.ks;
+    g.gk = 16 * g.ks;
+    return g;
+}
+
+// Tile order: double-float tiles (the X^T X block of S^T S) first, then the float32 tiles.
+__device__ MxTile mx_tile(const Blocks3& S, int q, int idx) {
+    const int T = (q + kTM - 1) / kTM;
+    const int xt = (S.w[0] + kTM - 1) / kTM;
+    int u = idx;
+    for (int ti = 0; ti < xt; ++ti)
+        for (int tj = ti; tj < xt; ++tj) {
+            if (u == 0) return MxTile{ti, tj, false, true};
+            --u;
+        }
+    for (int ti = 0; ti < T; ++ti)
+        for (int tj = 0; tj < T; ++tj)
+            if (mx_a_needed(S, q, ti, tj)) {
+                if (u == 0) return MxTile{ti, tj, true, false};
+                --u;
+            }
+    for (int ti = 0; ti < T; ++ti)
+        for (int tj = ti; tj < T; ++tj) {
+            if (ti < xt && tj < xt) continue;
+            if (u == 0) return MxTile{ti, tj, false, false};
+            --u;
+        }
+    return MxTile{0, 0, false, false};
+}
+
+// S.p = {Xh, W, P}, T.p = {R, AW, AP}; Xl = low plane of X.
+__global__ void __launch_bounds__(kGramMaxThreads)
+    k_gram_mx(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 Tb, const float* __restrict__ Xl,
+              double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float* sm = reinterpret_cast<float*>(sm_raw);
+    const int q = S.q();
+    const int T = (q + kTM - 1) / kTM;
+    const GramShape gs = mx_shape(S);
+    const int nt = gs.ntA + gs.ntB;
+    const int ldsm = T * kTM + 1;
+    const int plane = gs.gk * ldsm;
+    float* sS = sm;              // S (X hi)
+    float* sL = sm + plane;      // X lo (columns < w0)
+    float* sT = sm + 2 * plane;  // T
+    const int tile = threadIdx.x % nt;
+    const int grp = threadIdx.x / nt;
+    const bool active = grp < gs.ks;
+    const MxTile mt = mx_tile(S, q, tile);
+    const int ti = mt.ti, tj = mt.tj;
+    const int w0 = S.w[0];
+
+    float st_[kTM][kTM], tot[kTM][kTM], cmp[kTM][kTM];
+#pragma unroll
+    for (int a = 0; a < kTM; ++a)
+#pragma unroll
+        for (int b = 0; b < kTM; ++b) st_[a][b] = tot[a][b] = cmp[a][b] = 0.f;
+
+    const int64_t r0 = blockIdx.x * rows_per_part;
+    const int64_t r1 = min(n, r0 + rows_per_part);
+    const float* rhs = mt.isA ? sT : sS;
+    const int nload = gs.gk * T * kTM;
+    for (int64_t base = r0; base < r1; base += gs.gk) {
+        for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+            const int c = e / gs.gk, k = e - c * gs.gk;
+            const int64_t p = base + k;
+            float vs = 0.f, vl = 0.f, vt = 0.f;
+            if (c < q && p < r1) {
+                vs = load_col<float, float, float>(S, c, p);
+                vt = load_col<float, float, float>(Tb, c, p);
+                if (c < w0) vl = __ldg(Xl + (int64_t)c * S.ld + p);
+            }
+            sS[k * ldsm + c] = vs;
+            sL[k * ldsm + c] = vl;
+            sT[k * ldsm + c] = vt;
+        }
+        __syncthreads();
+        if (active) {
+            if (mt.df) {
+                for (int k = grp; k < gs.gk; k += gs.ks) {
+                    float xh[kTM], xl[kTM], yh[kTM], yl[kTM];
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u) {
+                        xh[u] = sS[k * ldsm + ti * kTM + u];
+                        xl[u] = sL[k * ldsm + ti * kTM + u];
+                        yh[u] = sS[k * ldsm + tj * kTM + u];
+                        yl[u] = sL[k * ldsm + tj * kTM + u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                        for (int v = 0; v < kTM; ++v) {
+                            const float pr = xh[u] * yh[v];
+                            float err = fmaf(xh[u], yh[v], -pr);
+                            err = fmaf(xh[u], yl[v], err);
+                            err = fmaf(xl[u], yh[v], err);
+                            const float t = tot[u][v] + pr;
+                            const float z = t - tot[u][v];
+                            const float d = (tot[u][v] - (t - z)) + (pr - z);
+                            tot[u][v] = t;
+                            cmp[u][v] += d + err;
+                        }
+                }
+            } else {
+                for (int k = grp; k < gs.gk; k += gs.ks) {
+                    float a[kTM], b[kTM];
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u) {
+                        a[u] = sS[k * ldsm + ti * kTM + u];
+                        b[u] = rhs[k * ldsm + tj * kTM + u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                        for (int v = 0; v < kTM; ++v) st_[u][v] = fmaf(a[u], b[v], st_[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                    for (int v = 0; v < kTM; ++v) {
+                        const float y = st_[u][v] - cmp[u][v];
+                        const float t = tot[u][v] + y;
+                        cmp[u][v] = (t - tot[u][v]) - y;
+                        tot[u][v] = t;
+                        st_[u][v] = 0.f;
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    double res[kTM][kTM];
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v)
+            res[u][v] = mt.df ? (double)tot[u][v] + (double)cmp[u][v] : (double)tot[u][v] - (double)cmp[u][v];
+    if (gs.ks > 1) {
+        double* red = reinterpret_cast<double*>(sm_raw);
+        if (active)
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int u = 0; u < kTM; ++u)
+#pragma unroll
+                for (int v = 0; v < kTM; ++v) {
+                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
+                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
+                    res[u][v] = sum;
+                }
+        }
+    }
+    if (grp != 0) return;
+    double* out = part + (int64_t)blockIdx.x * 2 * q * q + (mt.isA ? 0 : (int64_t)q * q);
+#pragma unroll
+    for (int u = 0; u < kTM; ++u)
+#pragma unroll
+        for (int v = 0; v < kTM; ++v) {
+            const int i = ti * kTM + u, j = tj * kTM + v;
+            if (i < q && j < q) out[i + (int64_t)q * j] = res[u][v];
+        }
+}
+
+// gramA / gramB of the mixed form from the partials of k_gram_mx (one warp per pair i <= j).
+__global__ void k_gram_finalize_mx(int q, int nparts, const double* __restrict__ part,
+                                   double* __restrict__ gA, double* __restrict__ gB,
+                                   const double* __restrict__ lam, Blocks3 W) {
+    const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = (int64_t)q * (q + 1) / 2;
+    if (pair >= npairs) return;
+    int j = 0;
+    int64_t u = pair;
+    while (u >= j + 1) { u -= j + 1; ++j; }
+    const int i = (int)u;
+    const int bi = block_of(W, i), bj = block_of(W, j);
+    const int64_t q2 = (int64_t)q * q;
+    // entries written by k_gram_mx: (i, j) when column j is in X or 1 <= block(i) <= block(j)
+    const bool need_ij = (bj == 0) || (bi >= 1);
+    const bool need_ji = (bi == 0) || (bi == bj);
+    double sb = 0.0, tij = 0.0, tji = 0.0;
+    for (int c = lane; c < nparts; c += 32) {
+        const double* P = part + (int64_t)c * 2 * q2;
+        sb += P[q2 + i + (int64_t)q * j];
+        if (need_ij) tij += P[i + (int64_t)q * j];
+        if (need_ji) tji += P[j + (int64_t)q * i];
+    }
+    sb = warp_sum(sb);
+    tij = warp_sum(tij);
+    tji = warp_sum(tji);
+    if (lane) return;
+    double a;
+    if (bi == 0 && bj == 0) a = 0.5 * (sb * (lam[i] + lam[j]) + tij + tji);
+    else if (bi == 0) a = lam[i] * sb + tji;           // (AX)^T s_j = lambda_i x_i^T s_j + r_i^T s_j
+    else if (bi == bj) a = 0.5 * (tij + tji);
+    else a = tij;
+    gA[i + (int64_t)q * j] = a;
+    gA[j + (int64_t)q * i] = a;
+    gB[i + (int64_t)q * j] = sb;
+    gB[j + (int64_t)q * i] = sb;
 }
 
 // One warp per unordered pair (i <= j): fixed-order sums of the partials.  gramA(i, j) is the
@@ -542,8 +778,8 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
 // S0 is float64; S1, S2 have type TW.  Each thread owns one grid point and kCG output columns.
 template <typename TW, typename CW>
 __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__ C,
-                         double* Xout, TW* Pout, int64_t ldout, const unsigned* __restrict__ status,
-                         unsigned skip) {
+                         double* Xout, TW* Pout, float* Xh, float* Xl, int64_t ldout,
+                         const unsigned* __restrict__ status, unsigned skip) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     double* sC = reinterpret_cast<double*>(sm_raw);             // q x m, column-major
     const int q = S.q();
@@ -591,7 +827,13 @@ __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__
             for (int c = 0; c < kCG; ++c) {
                 if (c0 + c < m) {
                     if (Pout) st_as(Pout + (int64_t)(c0 + c) * ldout + p, accP[c]);
-                    Xout[(int64_t)(c0 + c) * ldout + p] = accX[c] + (double)accP[c];
+                    const double xn = accX[c] + (double)accP[c];
+                    Xout[(int64_t)(c0 + c) * ldout + p] = xn;
+                    if (Xh) {   // float32 hi / lo planes of X (mixed form)
+                        const float hi = (float)xn;
+                        Xh[(int64_t)(c0 + c) * ldout + p] = hi;
+                        Xl[(int64_t)(c0 + c) * ldout + p] = (float)(xn - (double)hi);
+                    }
                 }
             }
         }
@@ -671,7 +913,7 @@ void launch_norms_finalize(int ncols, int nchunks, const double* partial, double
 }
 
 int gram_parts(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 1024), 2 * kNumSMs));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 1024), 4 * kNumSMs));
 }
 
 int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n) * 2 * q * q; }
@@ -757,18 +999,19 @@ void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void*
 }
 
 void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* Xout, void* Pout,
-                   int64_t ldout, const unsigned* status, unsigned skip_mask, cudaStream_t st) {
+                   int64_t ldout, const unsigned* status, unsigned skip_mask, cudaStream_t st,
+                   float* Xh, float* Xl) {
     const int groups = (int)ceil_div(m, kCG);
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
     const bool f32 = (S.w[1] + S.w[2] > 0 ? S.t12 : DT_F64) == DT_F32;
     if (f32) {
         const size_t smem = (size_t)S.q() * m * (sizeof(double) + sizeof(float));
         k_update<float, float><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
-            n, m, S, C, Xout, (float*)Pout, ldout, status, skip_mask);
+            n, m, S, C, Xout, (float*)Pout, Xh, Xl, ldout, status, skip_mask);
     } else {
         const size_t smem = (size_t)S.q() * m * (2 * sizeof(double));
         k_update<double, double><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
-            n, m, S, C, Xout, (double*)Pout, ldout, status, skip_mask);
+            n, m, S, C, Xout, (double*)Pout, Xh, Xl, ldout, status, skip_mask);
     }
     LG_CHECK_LAUNCH();
 }
@@ -776,13 +1019,35 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
 }  // namespace lg
 
 namespace lg {
-void launch_project(int64_t n, int b, float* V, const double* S0, int w0, const float* S1, int w1,
+void launch_project(int64_t n, int b, float* V, const float* S0, int w0, const float* S1, int w1,
                     int64_t ld, const double* C, int ldc, cudaStream_t st) {
     if (b <= 0) return;
     const int groups = (int)ceil_div(b, kCG);
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
     const size_t smem = (size_t)(w0 + w1) * b * sizeof(float);
     k_project<<<(unsigned)blocks, dim3(32, groups), smem, st>>>(n, b, V, S0, w0, S1, w1, ld, C, ldc);
+    LG_CHECK_LAUNCH();
+}
+}  // namespace lg
+
+namespace lg {
+void launch_gram_mx(int64_t n, const Blocks3& S, const Blocks3& T, const float* Xl, double* part,
+                    int nparts, const double* lam, double* gramA, double* gramB, cudaStream_t st) {
+    const int q = S.q();
+    const int TT = (q + kTM - 1) / kTM;
+    const GramShape gs = mx_shape(S);
+    const int nt = gs.ntA + gs.ntB;
+    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
+    LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
+    const size_t stage = 3 * (size_t)gs.gk * (TT * kTM + 1) * sizeof(float);
+    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
+    const size_t smem = std::max(stage, red);
+    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
+    const int64_t rows = ceil_div(n, nparts);
+    k_gram_mx<<<nparts, threads, smem, st>>>(n, rows, S, T, Xl, part);
+    LG_CHECK_LAUNCH();
+    const int64_t wthreads = (int64_t)q * (q + 1) / 2 * 32;
+    k_gram_finalize_mx<<<(unsigned)ceil_div(wthreads, 256), 256, 0, st>>>(q, nparts, part, gramA, gramB, lam, S);
     LG_CHECK_LAUNCH();
 }
 }  // namespace lg

@@ -113,25 +113,20 @@ __global__ void __launch_bounds__(kTX* kTY)
 
 // Trilinear prolongation: fine index f (1-based) takes coarse f/2 with weight 1 when f is
 // even, coarse (f-1)/2 and (f+1)/2 with weight 1/2 each when f is odd; coarse indices 0
-// and nc+1 are boundary zeros.
-struct Taps {
-    int idx[2];
-    float w[2];
-    int n;
-};
-__device__ inline Taps taps1d(int f0, int nc) {
-    Taps t;
+// and nc+1 are boundary zeros.  Per axis: two taps (index, weight), weight 0 when absent.
+__device__ __forceinline__ void taps1d(int f0, int nc, int& i0, int& i1, float& w0, float& w1) {
     const int f = f0 + 1;
-    t.n = 0;
     if ((f & 1) == 0) {
         const int I = f >> 1;
-        if (I <= nc) { t.idx[t.n] = I - 1; t.w[t.n] = 1.0f; ++t.n; }
+        i0 = I - 1; w0 = I <= nc ? 1.0f : 0.0f;
+        i1 = i0;    w1 = 0.0f;
     } else {
         const int I1 = (f - 1) >> 1, I2 = (f + 1) >> 1;
-        if (I1 >= 1) { t.idx[t.n] = I1 - 1; t.w[t.n] = 0.5f; ++t.n; }
-        if (I2 <= nc) { t.idx[t.n] = I2 - 1; t.w[t.n] = 0.5f; ++t.n; }
+        i0 = I1 - 1; w0 = I1 >= 1 ? 0.5f : 0.0f;
+        i1 = I2 - 1; w1 = I2 <= nc ? 0.5f : 0.0f;
     }
-    return t;
+    i0 = max(0, min(i0, nc - 1));   // clamp: a zero-weight tap still reads in bounds
+    i1 = max(0, min(i1, nc - 1));
 }
 
 template <typename TC, typename TF>
@@ -145,13 +140,20 @@ __global__ void __launch_bounds__(kTX* kTY)
     const int k = blockIdx.z - col * gf.nz;
     if (i >= gf.nx || j >= gf.ny) return;
     const TC* c = ec + (int64_t)col * ldc;
-    const Taps tx = taps1d(i, gc.nx), ty = taps1d(j, gc.ny), tz = taps1d(k, gc.nz);
+    int xi[2], yi[2], zi[2];
+    float xw[2], yw[2], zw[2];
+    taps1d(i, gc.nx, xi[0], xi[1], xw[0], xw[1]);
+    taps1d(j, gc.ny, yi[0], yi[1], yw[0], yw[1]);
+    taps1d(k, gc.nz, zi[0], zi[1], zw[0], zw[1]);
     C s = 0;
-    for (int a = 0; a < tz.n; ++a)
-        for (int b = 0; b < ty.n; ++b) {
-            const C w = C(tz.w[a]) * C(ty.w[b]);
-            const int64_t row = (int64_t)gc.nx * (ty.idx[b] + (int64_t)gc.ny * tz.idx[a]);
-            for (int d = 0; d < tx.n; ++d) s = fma(w * C(tx.w[d]), C(ld_as(c + row + tx.idx[d])), s);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const C w = C(zw[a]) * C(yw[b]);
+            const int64_t row = (int64_t)gc.nx * (yi[b] + (int64_t)gc.ny * zi[a]);
+#pragma unroll
+            for (int d = 0; d < 2; ++d) s = fma(w * C(xw[d]), C(ld_as(c + row + xi[d])), s);
         }
     const int64_t p = (int64_t)col * ldf + i + (int64_t)gf.nx * (j + (int64_t)gf.ny * k);
     const C old = ld_as(ef + p);

@@ -72,6 +72,7 @@ struct lobpcg_handle {
     int64_t ld = 0;
     Buf X, AX;                                  // float64
     Buf W, AW, P, AP, Pc, APc, E0, T0;          // type tw
+    Buf Xh, Xl, R;                              // mixed form: float32 planes of X, residual block
     std::vector<Buf> lr, le, lt;                // type tl
     std::vector<int64_t> lld;
     Buf part;          // Gram / residual partial sums
@@ -93,6 +94,8 @@ struct lobpcg_handle {
     bool pending_check = false;
     std::vector<int> J;
     std::vector<double> lam_h, norms_h, resid_h;
+    std::vector<int> norm_cols;                 // columns whose norms the last residual pass computed
+    std::vector<double> norm_by_col;            // those norms, indexed by column
     int p_dropped = 0;
     int fp64_sweeps = 0;
     double setup_ms = 0.0, solve_ms = 0.0;
@@ -140,7 +143,7 @@ int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 void free_workspace(lobpcg_t* h) {
     for (Buf* b : {&h->X, &h->AX, &h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0,
-                   &h->part, &h->small})
+                   &h->Xh, &h->Xl, &h->R, &h->part, &h->small})
         dfree(h, *b);
     for (auto& b : h->lr) dfree(h, b);
     for (auto& b : h->le) dfree(h, b);
@@ -164,6 +167,8 @@ void ensure_workspace(lobpcg_t* h, int wm) {
     ensure(h, h->X, blk64);
     ensure(h, h->AX, blk64);
     for (Buf* b : {&h->W, &h->AW, &h->P, &h->AP, &h->Pc, &h->APc, &h->E0, &h->T0}) ensure(h, *b, blkw);
+    if (h->precision == LOBPCG_MIXED)
+        for (Buf* b : {&h->Xh, &h->Xl, &h->R}) ensure(h, *b, (size_t)h->ld * wm * sizeof(float));
     const int L = (int)h->lv.size();
     h->lr.assign(L, Buf{});
     h->le.assign(L, Buf{});
@@ -315,12 +320,12 @@ void project_out(lobpcg_t* h, int b, void* V, const void* W) {
     const int q = m + wb + b;
     const int nparts = gram_parts(n);
     for (int pass = 0; pass < 2; ++pass) {
-        const Blocks3 S = blocks(h->X.p, m, DT_F64, W ? W : V, W ? b : b, V, W ? b : 0, DT_F32, h->ld);
+        const Blocks3 S = blocks(h->Xh.p, m, DT_F32, W ? W : V, b, V, W ? b : 0, DT_F32, h->ld);
         launch_gram_f32(n, S, f64(h->part), nparts, h->stream);
         launch_gram_finalize(q, nparts, f64(h->part), false, nullptr, h->gramB, nullptr, &S, h->stream);
         // coefficients: rows 0 .. m + wb - 1 of the last b columns of gramB
-        launch_project(n, b, static_cast<float*>(V), f64(h->X), m, static_cast<const float*>(W), wb, h->ld,
-                       h->gramB + (size_t)(m + wb) * q, q, h->stream);
+        launch_project(n, b, static_cast<float*>(V), static_cast<const float*>(h->Xh.p), m,
+                       static_cast<const float*>(W), wb, h->ld, h->gramB + (size_t)(m + wb) * q, q, h->stream);
     }
 }
 
@@ -341,28 +346,37 @@ void events_create(lobpcg_t* h) {
 
 // ------------------------------------------------------------------ the iteration
 void residual_into_W(lobpcg_t* h) {
-    // step 7 for the current J: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]], norms to host
+    // step 7: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]] and the norms (to the host).  The
+    // mixed form computes the residual R of all m columns (its Gram uses R for every column).
     const int64_t n = h->g.n();
+    const bool mixed = h->precision == LOBPCG_MIXED;
     ColList cols{};
-    cols.n = (int)h->J.size();
-    for (int t = 0; t < cols.n; ++t) cols.idx[t] = h->J[t];
-    launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, h->tw, h->W.p, h->ld, f64(h->part),
-                    h->stream);
+    if (mixed) {
+        cols = identity_cols(h->m);
+    } else {
+        cols.n = (int)h->J.size();
+        for (int t = 0; t < cols.n; ++t) cols.idx[t] = h->J[t];
+    }
+    h->norm_cols.assign(cols.idx, cols.idx + cols.n);
+    launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, h->tw, mixed ? h->R.p : h->W.p, h->ld,
+                    f64(h->part), h->stream);
     launch_norms_finalize(cols.n, residual_chunks(n), f64(h->part), h->norms, h->stream);
 }
 
 // Copy the small per-iteration results to the host: norms of J, lambda, status word.
 unsigned fetch_small(lobpcg_t* h) {
     unsigned st = 0;
-    h->norms_h.resize(h->J.size());
-    if (!h->J.empty())
-        LG_CUDA(cudaMemcpyAsync(h->norms_h.data(), h->norms, h->J.size() * sizeof(double),
+    h->norms_h.resize(h->norm_cols.size());
+    if (!h->norm_cols.empty())
+        LG_CUDA(cudaMemcpyAsync(h->norms_h.data(), h->norms, h->norm_cols.size() * sizeof(double),
                                 cudaMemcpyDeviceToHost, h->stream));
     h->lam_h.resize(h->m);
     LG_CUDA(cudaMemcpyAsync(h->lam_h.data(), h->lam, h->m * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
     LG_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LG_CUDA(cudaStreamSynchronize(h->stream));
+    h->norm_by_col.assign(h->m, 0.0);
+    for (size_t t = 0; t < h->norm_cols.size(); ++t) h->norm_by_col[h->norm_cols[t]] = h->norms_h[t];
     return st;
 }
 
@@ -383,7 +397,9 @@ void orthonormalize_and_rr(lobpcg_t* h) {
     launch_rayleigh_ritz(m, m, m, h->gramA, nullptr, h->lam, h->Cm, h->rrwork, h->status,
                          ST_X_BREAKDOWN, st);
     const unsigned skip = ST_X_BREAKDOWN | ST_RR_BREAKDOWN;
-    launch_update(n, m, SX, h->Cm, f64(h->X), nullptr, h->ld, h->status, skip, st);
+    float* xh = h->precision == LOBPCG_MIXED ? static_cast<float*>(h->Xh.p) : nullptr;
+    float* xl = h->precision == LOBPCG_MIXED ? static_cast<float*>(h->Xl.p) : nullptr;
+    launch_update(n, m, SX, h->Cm, f64(h->X), nullptr, h->ld, h->status, skip, st, xh, xl);
     launch_update(n, m, SAX, h->Cm, f64(h->AX), nullptr, h->ld, h->status, skip, st);
     h->J.resize(m);
     for (int j = 0; j < m; ++j) h->J[j] = j;
@@ -443,9 +459,13 @@ bool check_and_lock(lobpcg_t* h) {
     for (size_t t = 0; t < h->J.size(); ++t) {
         const int j = h->J[t];
         const double bound = h->tol_mode == LOBPCG_TOL_RELATIVE ? h->tol * std::fabs(h->lam_h[j]) : h->tol;
-        if (!(h->norms_h[t] <= bound)) keep.push_back((int)t);
+        if (!(h->norm_by_col[j] <= bound)) keep.push_back((int)t);
     }
-    if (keep.size() != h->J.size()) {
+    if (keep.size() != h->J.size() && h->precision == LOBPCG_MIXED) {
+        std::vector<int> nJ;
+        for (int t : keep) nJ.push_back(h->J[t]);
+        h->J.swap(nJ);
+    } else if (keep.size() != h->J.size()) {
         // compact the residual block W to the surviving columns
         std::vector<int> nJ;
         const size_t es = dtype_size(h->tw);
@@ -469,10 +489,21 @@ void pass_body(lobpcg_t* h) {
     cudaStream_t st = h->stream;
     PhaseTimer tm(h);
     tm.mark(0);
-    // step 9: W_J = T W_J (output in E0, then the buffers swap roles)
-    precond(h, b, tw, h->W.p, ld, h->E0.p, ld, h->T0.p, ld);
-    std::swap(h->W, h->E0);
+    // step 9: W_J = T W_J (output in E0, then the buffers swap roles).  The mixed form keeps the
+    // residuals of all columns in R and preconditions R[:, J].
     const bool mixed = h->precision == LOBPCG_MIXED;
+    const void* rin = h->W.p;
+    if (mixed) {
+        if (b == m) {
+            rin = h->R.p;
+        } else {
+            for (int t = 0; t < b; ++t)
+                LG_CUDA(cudaMemcpyAsync(col(h->W, tw, ld, t), col(h->R, tw, ld, h->J[t]), n * dtype_size(tw),
+                                        cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
+    std::swap(h->W, h->E0);
     if (mixed) project_out(h, b, h->W.p, nullptr);
     tm.mark(1);
     // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
@@ -520,7 +551,16 @@ void pass_body(lobpcg_t* h) {
     const Blocks3 S = blocks(h->X.p, m, DT_F64, h->W.p, b, Pj, use_p ? b : 0, tw, ld);
     const Blocks3 AS = blocks(h->AX.p, m, DT_F64, h->AW.p, b, APj, use_p ? b : 0, tw, ld);
     const int q = S.q();
-    gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
+    if (mixed) {
+        const Blocks3 SH = blocks(h->Xh.p, m, DT_F32, h->W.p, b, Pj, use_p ? b : 0, DT_F32, ld);
+        const Blocks3 TR = blocks(h->R.p, m, DT_F32, h->AW.p, b, APj, use_p ? b : 0, DT_F32, ld);
+        const int nparts = gram_parts(n);
+        LG_REQUIRE((size_t)nparts * 2 * q * q <= h->part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
+        launch_gram_mx(n, SH, TR, static_cast<const float*>(h->Xl.p), f64(h->part), nparts, h->lam,
+                       h->gramA, h->gramB, st);
+    } else {
+        gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
+    }
     tm.mark(5);
     // step 24: gramA C = gramB C Lambda (P block dropped on device if needed)
     launch_rayleigh_ritz(q, m + b, m, h->gramA, h->gramB, h->lam, h->Cm, h->rrwork, h->status,
@@ -528,7 +568,8 @@ void pass_body(lobpcg_t* h) {
     tm.mark(6);
     // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
     const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
-    launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st);
+    launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st,
+                  mixed ? static_cast<float*>(h->Xh.p) : nullptr, mixed ? static_cast<float*>(h->Xl.p) : nullptr);
     if (mixed) {
         // Mixed form: AX = A X by a float64 SpMV (cheaper than the float64 update AX C_X, and
         // free of the drift that float32 AP would add to an implicitly updated AX).  AP is
