@@ -478,11 +478,13 @@ __global__ void k_project(int64_t n, int b, float* V, const float* __restrict__ 
         float acc[kCG];
 #pragma unroll
         for (int c = 0; c < kCG; ++c) acc[c] = 0.f;
+#pragma unroll 8
         for (int i = 0; i < w0; ++i) {
             const float v = __ldg(S0 + (int64_t)i * ld + p);
 #pragma unroll
             for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[i + r * min(c0 + c, b - 1)], acc[c]);
         }
+#pragma unroll 8
         for (int i = 0; i < w1; ++i) {
             const float v = __ldg(S1 + (int64_t)i * ld + p);
 #pragma unroll
@@ -804,19 +806,22 @@ __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__
 #pragma unroll
         for (int c = 0; c < kCG; ++c) { accP[c] = CW(0); accX[c] = 0.0; }
         if (valid) {
+#pragma unroll 8
             for (int i = 0; i < w1; ++i) {
                 const CW v = (CW)ld_as(S1 + (int64_t)i * ld + p);
 #pragma unroll
                 for (int c = 0; c < kCG; ++c) accP[c] = fma(v, sCw[(w0 + i) + q * min(c0 + c, m - 1)], accP[c]);
             }
+#pragma unroll 8
             for (int i = 0; i < w2; ++i) {
                 const CW v = (CW)ld_as(S2 + (int64_t)i * ld + p);
 #pragma unroll
                 for (int c = 0; c < kCG; ++c)
                     accP[c] = fma(v, sCw[(w0 + w1 + i) + q * min(c0 + c, m - 1)], accP[c]);
             }
+#pragma unroll 8
             for (int i = 0; i < w0; ++i) {
-                const double v = S0[(int64_t)i * ld + p];
+                const double v = __ldg(S0 + (int64_t)i * ld + p);
 #pragma unroll
                 for (int c = 0; c < kCG; ++c) accX[c] = fma(v, sC[i + q * min(c0 + c, m - 1)], accX[c]);
             }
@@ -861,6 +866,7 @@ __global__ void k_apply_upper(int64_t n, int b, const T* Vin, int64_t ldin, T* V
 #pragma unroll
         for (int c = 0; c < kCG; ++c) acc[c] = C(0);
         if (valid) {
+#pragma unroll 8
             for (int i = 0; i < iend; ++i) {
                 const C v = (C)Vin[(int64_t)i * ldin + p];
 #pragma unroll
