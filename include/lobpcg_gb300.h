@@ -226,6 +226,34 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
  * <= b * 2^-52. */
 int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld);
 
+/* Mixed form, float32 Gram products (Algorithm steps 11 and 13 and the block
+ * Gram-Schmidt projections of W and P that the mixed form adds): with float32
+ * device blocks S0 (w0 columns), S1 (w1 columns, may be NULL when w1 = 0) and V
+ * (b columns), each n rows with the common leading dimension ld (a multiple of
+ * 4; pointers 16-byte aligned), writes C = [S0 S1]^T V ((w0 + w1)-by-b,
+ * column-major, ld w0 + w1; skipped if C is NULL or w0 + w1 = 0) and
+ * G = V^T V (b-by-b, symmetric; skipped if NULL), both float64 on the device.
+ * Float32 products, compensated float32 sums, float64 partial sums added in a
+ * fixed order.  w0 + w1 <= 2 * LOBPCG_MAX_M, b <= LOBPCG_MAX_M. */
+int lobpcg_op_gram_f32(lobpcg_t* h, const float* S0, int w0, const float* S1, int w1,
+                       const float* V, int b, int64_t ld, double* C, double* G);
+
+/* Mixed form, Gram matrices in residual form (Algorithm steps 17-23): basis
+ * S = [X W P] with X given as float32 planes (X = Xh + Xl), W (b columns) and
+ * P (bp columns, bp = 0: no P block), and T = [R AW AP] with R = AX - X Lambda
+ * (Lambda = diag(lambda), lambda: device, m values); all float32 device blocks,
+ * n rows, common leading dimension ld (a multiple of 4, 16-byte aligned).
+ * Writes gramB = S^T S and gramA = S^T (AS) (q-by-q, q = m + b + bp,
+ * column-major, device) with X^T AX = (X^T X) Lambda + X^T R symmetrised,
+ * (AX)^T S_j = Lambda X^T S_j + R^T S_j, the upper block triangle S_I^T AS_J of
+ * the W / P part (I < J) and (S_I^T AS_I + AS_I^T S_I) / 2 on its diagonal
+ * blocks.  X^T X in double-float arithmetic (hi * hi products exact, about
+ * 2^-44 relative), all other products float32 with compensated sums. */
+int lobpcg_op_gram_residual(lobpcg_t* h, const float* Xh, const float* Xl, const float* W,
+                            const float* P, const float* R, const float* AW, const float* AP,
+                            int64_t ld, int m, int b, int bp, const double* lambda,
+                            double* gramA, double* gramB);
+
 /* Rayleigh-Ritz (Algorithm step 24) on device matrices: gramA C = gramB C Lambda
  * for q-by-q symmetric gramA, gramB (column-major), the m smallest eigenvalues
  * ascending into device lambda and the gramB-orthonormal eigenvectors into

@@ -62,6 +62,10 @@ _SIGNATURES = {
                                    c_void_p, c_void_p, c_int64, c_void_p]),
     "lobpcg_op_gram": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_int64, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "lobpcg_op_gram_f32": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_int64,
+                                   c_void_p, c_void_p]),
+    "lobpcg_op_gram_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_int64, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "lobpcg_op_cholqr": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int64]),
     "lobpcg_op_rayleigh_ritz": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lobpcg_gram_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
@@ -164,6 +168,14 @@ def lobpcg_op_residual(h, ncols, cols, X, AX, ld, lam, W, ldw, norms):
 
 def lobpcg_op_gram(h, S0, S1, S2, AS0, AS1, AS2, ld, w0, w1, w2, gramA, gramB):
     return _call("lobpcg_op_gram", h, S0, S1, S2, AS0, AS1, AS2, ld, w0, w1, w2, gramA, gramB)
+
+
+def lobpcg_op_gram_f32(h, S0, w0, S1, w1, V, b, ld, C, G):
+    return _call("lobpcg_op_gram_f32", h, S0, w0, S1, w1, V, b, ld, C, G)
+
+
+def lobpcg_op_gram_residual(h, Xh, Xl, W, P, R, AW, AP, ld, m, b, bp, lam, gramA, gramB):
+    return _call("lobpcg_op_gram_residual", h, Xh, Xl, W, P, R, AW, AP, ld, m, b, bp, lam, gramA, gramB)
 
 
 def lobpcg_op_cholqr(h, b, V, AV, ld):

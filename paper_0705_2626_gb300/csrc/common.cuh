@@ -64,6 +64,7 @@ enum StatusBits : unsigned {
     ST_RR_BREAKDOWN = 4u,     // gramB not positive definite without P
     ST_X_BREAKDOWN = 8u,      // chol(X^T X) failed (step 3)
     ST_NONFINITE = 16u,       // non-finite value in a small dense matrix
+    ST_TIMEOUT = 32u,         // a bounded wait of a kernel gave up (its results are invalid)
 };
 
 // Storage types of the blocks: float64 (FP64 form; X and AX of the mixed form), float32 (the
@@ -117,15 +118,12 @@ struct Blocks3 {
     DType t0, t12;
     __host__ __device__ int q() const { return w[0] + w[1] + w[2]; }
 };
-// Gram partial sums over `nparts` row ranges: part has nparts * 2*q*q doubles.  Float64
-// blocks only: float64 arithmetic; otherwise float32 products with compensated sums.
+// Gram partial sums over `nparts` row ranges: part has nparts * 2*q*q doubles; float64 blocks
+// and arithmetic (the float32 Grams of the mixed form are in k_gram32.cu).
 int gram_parts(int64_t n);
 int64_t gram_scratch_doubles(int64_t n, int q);
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st);
-// S^T S partials in plain float32 products (block 0 may be float64, converted on load): the
-// projection coefficients of the mixed form, where float32 accuracy suffices.
-void launch_gram_f32(int64_t n, const Blocks3& S, double* part, int nparts, cudaStream_t st);
 // gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
 // summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
 // diagonal blocks of gramB are identities (steps 18-22 as printed).
@@ -147,15 +145,53 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
                    void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
                    cudaStream_t st, float* Xh = nullptr, float* Xl = nullptr);
 
-// Mixed form, block Gram-Schmidt: V -= S0 C[0:w0, :] + S1 C[w0:w0+w1, :] (V, S0 = the float32
-// plane of X, S1 float32; C float64 with leading dimension ldc), float32 arithmetic.
-void launch_project(int64_t n, int b, float* V, const float* S0, int w0, const float* S1, int w1,
-                    int64_t ld, const double* C, int ldc, cudaStream_t st);
-// Mixed-form Gram in residual form (S = [X W P] with X as float32 hi plane S.p[0] and lo plane
-// Xl, T = [R AW AP], R = AX - X Lambda): writes gramA and gramB (q x q) using lam = Lambda.
-void launch_gram_mx(int64_t n, const Blocks3& S, const Blocks3& T, const float* Xl, double* part,
-                    int nparts, const double* lam, double* gramA, double* gramB, cudaStream_t st);
-
+// gramA / gramB of the residual form from its partial sums (nparts chunks of 2 q^2 doubles,
+// q = m + b + bp; see launch_gram_mx2).
+void launch_gram_finalize_mx(int q, int m, int b, int bp, int nparts, const double* part,
+                             const double* lam, double* gramA, double* gramB, cudaStream_t st);
+// ---------------------------------------------------------------- TMA-staged float32 Grams
+// (k_gram32.cu).  Blocks are float32, 16-byte aligned, with a common leading dimension ld
+// divisible by 4.  Partial sums go to `part` (g32_chunks(n) chunks; part_doubles is checked).
+// A kernel whose bounded wait gives up sets ST_TIMEOUT in *status.
+int g32_chunks(int64_t n);
+// C = [S0 S1]^T V ((w0 + w1) x b, column-major, ld w0 + w1) and, if G != null, G = V^T V
+// (b x b, symmetric): float32 products, compensated float32 sums, float64 chunk sums.
+void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const float* S1, int w1,
+                         const float* V, int b, double* C, double* G, double* part,
+                         int64_t part_doubles, unsigned* status, cudaStream_t st);
+// Residual-form Gram of the mixed form, S = [X W P] (X as hi / lo planes Xh, Xl), T = [R AW AP]
+// (R = AX - X Lambda): float32 tiles for every block but X^T X, double-float tiles for X^T X,
+// then gramA, gramB (q x q, q = m + b + bp) as in launch_gram_mx.
+void launch_gram_mx2(int64_t n, int64_t ld, const float* Xh, const float* Xl, const float* W,
+                     const float* P, const float* R, const float* AW, const float* AP, int m, int b,
+                     int bp, double* part, int64_t part_doubles, const double* lam, double* gramA,
+                     double* gramB, unsigned* status, cudaStream_t st);
+// ---------------------------------------------------------------- mixed form, X as planes
+// (k_mixed.cu).  X = Xh + Xl (float32 hi / lo planes, ld divisible by 4).
+// R = A X - X diag(lam) (double-float stencil, R float32) for m columns, and per-block sums of
+// squares: partial[j * resid_mx_blocks(g) + block] (add them with launch_norms_finalize).
+int resid_mx_blocks(const Grid3& g);
+void launch_resid_mx(const Grid3& g, int m, double scale, const float* Xh, const float* Xl,
+                     int64_t ld, const double* lam, float* R, int64_t ldr, double* partial,
+                     cudaStream_t st);
+// X = Xh + Xl in float64.
+void launch_planes_to_f64(int64_t n, int m, const float* Xh, const float* Xl, int64_t ld, double* X,
+                          int64_t ldx, cudaStream_t st);
+// ---------------------------------------------------------------- TMA-streamed float32 products
+// (k_tsmm.cu).  Blocks float32, 16-byte aligned, ld divisible by 4; a kernel whose bounded wait
+// gives up sets ST_TIMEOUT in *err.
+// V <- V - [L0 L1] C for b columns of V (C (w0 + w1) x b, column-major, ld ldc, float64).
+void launch_project32(int64_t n, int b, float* V, const float* L0, int w0, const float* L1, int w1,
+                      int64_t ld, const double* C, int ldc, unsigned* err, cudaStream_t st);
+// V <- V Rinv (Rinv b x b upper triangular, ld b, float64), in place; skipped if *status & skip.
+void launch_apply32(int64_t n, int b, float* V, int64_t ld, const double* Rinv,
+                    const unsigned* status, unsigned skip, unsigned* err, cudaStream_t st);
+// Ritz update of the mixed form: Pout = W C_W + P C_P (float32) and X = X C_X + Pout in
+// double-float with X = Xh + Xl (in place), C q x m column-major (ld q) with rows C_X (m), C_W (b),
+// C_P (bp); Pout may alias P or be null.  Skipped if *status & skip.
+void launch_update_mx2(int64_t n, int m, float* Xh, float* Xl, const float* W, int b, const float* P,
+                       int bp, int64_t ld, const double* C, int q, float* Pout, const unsigned* status,
+                       unsigned skip, unsigned* err, cudaStream_t st);
 // ---------------------------------------------------------------- small dense
 // Rinv = R^-1, R = chol(G) on the unit-diagonal scaling of G (b x b).  On failure sets
 // fail_bit in *status and leaves Rinv unspecified.  Skipped if *status & skip_mask.

@@ -271,432 +271,11 @@ __global__ void __launch_bounds__(kGramMaxThreads)
         }
 }
 
-// Mixed-form Gram: block 0 (X, AX) float64, blocks 1-2 (W, P families) float32.  Tiles in the
-// X rows of the output (the blocks X^T AX, X^T AW, X^T AP, X^T X, X^T W, X^T P) are computed in
-// double-float arithmetic: every float64 entry is split into float32 hi + lo parts when it is
-// staged in shared memory, hi * hi products are made exact with an FMA, the hi * lo cross terms
-// are added, and the sums are kept as unevaluated float32 pairs (two-sum), about 2^-44 relative.
-// These blocks couple the float64 Ritz vectors with the float32 search directions; their
-// float32 roundings would otherwise not cancel (A W has large terms while X^T A W is small) and
-// would limit the attainable residual.  The remaining tiles (W and P only) use float32 products
-// summed per stage with Kahan compensation across stages.  Tiles are ordered double-float first.
-struct MixedTile {
-    int ti, tj;
-    bool isA, df;
-};
-
-__device__ MixedTile mixed_tile(const Blocks3& S, int q, int with_a, int idx) {
-    const int T = (q + kTM - 1) / kTM;
-    const int xrows = (S.w[0] + kTM - 1) / kTM;     // tile rows that touch X
-    MixedTile r{0, 0, false, false};
-    int u = idx;
-    for (int pass = 0; pass < 2; ++pass) {           // pass 0: double-float tiles, 1: float32
-        const bool df = pass == 0;
-        if (with_a)
-            for (int ti = 0; ti < T; ++ti) {
-                if ((ti < xrows) != df) continue;
-                for (int tj = 0; tj < T; ++tj)
-                    if (a_tile_needed(S, q, ti, tj)) {
-                        if (u == 0) return MixedTile{ti, tj, true, df};
-                        --u;
-                    }
-            }
-        for (int ti = 0; ti < T; ++ti) {
-            if ((ti < xrows) != df) continue;
-            for (int tj = ti; tj < T; ++tj) {
-                if (u == 0) return MixedTile{ti, tj, false, df};
-                --u;
-            }
-        }
-    }
-    return r;
-}
-
-__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
-}
-
-__global__ void __launch_bounds__(kGramMaxThreads)
-    k_gram_mixed(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
-                 double* __restrict__ part) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    float* sm = reinterpret_cast<float*>(sm_raw);
-    const int q = S.q();
-    const int T = (q + kTM - 1) / kTM;
-    const GramShape gs = gram_shape(S, with_a != 0, 16);   // 4 float planes per staged value
-    const int nt = gs.ntA + gs.ntB;
-    const int ldsm = T * kTM + 1;
-    const int plane = gs.gk * ldsm;
-    float* sSh = sm;
-    float* sSl = sm + plane;
-    float* sAh = sm + 2 * plane;
-    float* sAl = sm + 3 * plane;
-    const int tile = threadIdx.x % nt;
-    const int grp = threadIdx.x / nt;
-    const bool active = grp < gs.ks;
-    const MixedTile mt = mixed_tile(S, q, with_a, tile);
-    const int ti = mt.ti, tj = mt.tj;
-    const int w0 = S.w[0];
-
-    // double-float tiles: tot = hi, cmp = lo of the running sums; float32 tiles: st_ = the stage's
-    // sums, tot / cmp = Kahan sum and compensation
-    float st_[kTM][kTM], tot[kTM][kTM], cmp[kTM][kTM];
-#pragma unroll
-    for (int a = 0; a < kTM; ++a)
-#pragma unroll
-        for (int b = 0; b < kTM; ++b) st_[a][b] = tot[a][b] = cmp[a][b] = 0.f;
-
-    const int64_t r0 = blockIdx.x * rows_per_part;
-    const int64_t r1 = min(n, r0 + rows_per_part);
-    const float* rh = mt.isA ? sAh : sSh;
-    const float* rl = mt.isA ? sAl : sSl;
-    for (int64_t base = r0; base < r1; base += gs.gk) {
-        for (int e = threadIdx.x; e < gs.gk * T * kTM; e += blockDim.x) {
-            const int c = e / gs.gk, k = e - c * gs.gk;
-            const int64_t p = base + k;
-            float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
-            if (c < q && p < r1) {
-                if (c < w0) {
-                    split_f64(__ldg(static_cast<const double*>(S.p[0]) + (int64_t)c * S.ld + p), sh, sl);
-                    if (with_a) split_f64(__ldg(static_cast<const double*>(AS.p[0]) + (int64_t)c * AS.ld + p), ah, al);
-                } else {
-                    sh = load_col<double, float, float>(S, c, p);
-                    if (with_a) ah = load_col<double, float, float>(AS, c, p);
-                }
-            }
-            sSh[k * ldsm + c] = sh;
-            sSl[k * ldsm + c] = sl;
-            if (with_a) { sAh[k * ldsm + c] = ah; sAl[k * ldsm + c] = al; }
-        }
-        __syncthreads();
-        if (active) {
-            if (mt.df) {
-                for (int k = grp; k < gs.gk; k += gs.ks) {
-                    float xh[kTM], xl[kTM], yh[kTM], yl[kTM];
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u) {
-                        xh[u] = sSh[k * ldsm + ti * kTM + u];
-                        xl[u] = sSl[k * ldsm + ti * kTM + u];
-                        yh[u] = rh[k * ldsm + tj * kTM + u];
-                        yl[u] = rl[k * ldsm + tj * kTM + u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                        for (int v = 0; v < kTM; ++v) {
-                            const float p = xh[u] * yh[v];
-                            float err = fmaf(xh[u], yh[v], -p);
-                            err = fmaf(xh[u], yl[v], err);
-                            err = fmaf(xl[u], yh[v], err);
-                            const float t = tot[u][v] + p;          // two-sum of (hi, p)
-                            const float z = t - tot[u][v];
-                            const float d = (tot[u][v] - (t - z)) + (p - z);
-                            tot[u][v] = t;
-                            cmp[u][v] += d + err;
-                        }
-                }
-            } else {
-                for (int k = grp; k < gs.gk; k += gs.ks) {
-                    float a[kTM], b[kTM];
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u) {
-                        a[u] = sSh[k * ldsm + ti * kTM + u];
-                        b[u] = rh[k * ldsm + tj * kTM + u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                        for (int v = 0; v < kTM; ++v) st_[u][v] = fmaf(a[u], b[v], st_[u][v]);
-                }
-#pragma unroll
-                for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                    for (int v = 0; v < kTM; ++v) {
-                        const float y = st_[u][v] - cmp[u][v];
-                        const float t = tot[u][v] + y;
-                        cmp[u][v] = (t - tot[u][v]) - y;
-                        tot[u][v] = t;
-                        st_[u][v] = 0.f;
-                    }
-            }
-        }
-        __syncthreads();
-    }
-    double res[kTM][kTM];
-#pragma unroll
-    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-        for (int v = 0; v < kTM; ++v)
-            res[u][v] = mt.df ? (double)tot[u][v] + (double)cmp[u][v] : (double)tot[u][v] - (double)cmp[u][v];
-    if (gs.ks > 1) {
-        double* red = reinterpret_cast<double*>(sm_raw);   // [ks][nt][16]
-        if (active)
-#pragma unroll
-            for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
-        __syncthreads();
-        if (grp == 0) {
-#pragma unroll
-            for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                for (int v = 0; v < kTM; ++v) {
-                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
-                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
-                    res[u][v] = sum;
-                }
-        }
-    }
-    if (grp != 0) return;
-    double* out = part + (int64_t)blockIdx.x * 2 * q * q + (mt.isA ? 0 : (int64_t)q * q);
-#pragma unroll
-    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-        for (int v = 0; v < kTM; ++v) {
-            const int i = ti * kTM + u, j = tj * kTM + v;
-            if (i < q && j < q) out[i + (int64_t)q * j] = res[u][v];
-        }
-}
-
-// Block Gram-Schmidt step of the mixed form: V -= S0 C0 + S1 C1 for the b columns of V (float32),
-// S0 = float32 plane of X (w0 columns), S1 float32 (w1 columns: W, or none), C (w0 + w1) x b
-// column-major float64.  Float32 arithmetic; each thread owns one grid point and kCG columns of V.
-__global__ void k_project(int64_t n, int b, float* V, const float* __restrict__ S0, int w0,
-                          const float* __restrict__ S1, int w1, int64_t ld,
-                          const double* __restrict__ C, int ldc) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    float* sC = reinterpret_cast<float*>(sm_raw);        // (w0 + w1) x b
-    const int r = w0 + w1;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < r * b; e += 32 * blockDim.y)
-        sC[e] = (float)C[(e % r) + (int64_t)ldc * (e / r)];
-    __syncthreads();
-    const int c0 = threadIdx.y * kCG;
-    for (int64_t base = blockIdx.x * 32ll; base < n; base += (int64_t)gridDim.x * 32) {
-        const int64_t p = base + threadIdx.x;
-        if (p >= n) continue;
-        float acc[kCG];
-#pragma unroll
-        for (int c = 0; c < kCG; ++c) acc[c] = 0.f;
-#pragma unroll 8
-        for (int i = 0; i < w0; ++i) {
-            const float v = __ldg(S0 + (int64_t)i * ld + p);
-#pragma unroll
-            for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[i + r * min(c0 + c, b - 1)], acc[c]);
-        }
-#pragma unroll 8
-        for (int i = 0; i < w1; ++i) {
-            const float v = __ldg(S1 + (int64_t)i * ld + p);
-#pragma unroll
-            for (int c = 0; c < kCG; ++c) acc[c] = fmaf(v, sC[w0 + i + r * min(c0 + c, b - 1)], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < kCG; ++c)
-            if (c0 + c < b) {
-                float* vp = V + (int64_t)(c0 + c) * ld + p;
-                *vp = *vp - acc[c];
-            }
-    }
-}
-
-// Mixed-form Gram in residual form.  Basis S = [X W P] (X as float32 hi / lo planes, W and P
-// float32) and T = [R AW AP] with R = AX - X Lambda (float32; small near convergence).  Partial
-// sums of
-//   S^T T  at (i, j) for every row i of an X column j (X^T R, W^T R, P^T R) and for the upper
-//          block triangle of the W / P part (W^T AW, W^T AP, P^T AP);
-//   S^T S  upper triangle, the X^T X block in double-float arithmetic (hi * hi exact by FMA,
-//          hi * lo cross terms, two-sum accumulation), the rest in float32.
-// The finalize step forms gramA from them with (AX)^T S_j = Lambda X^T S_j + R^T S_j and
-// X^T AX = (X^T X) Lambda + X^T R, so no float32 product ever has to cancel a large term.
-// Float32 sums are compensated (Kahan) across stages of 16 rows per thread.
-struct MxTile {
-    int ti, tj;
-    bool isA, df;
-};
-
-__host__ __device__ inline bool mx_a_needed(const Blocks3& S, int q, int ti, int tj) {
-    const int cmin = block_of(S, tj * kTM), cmax = block_of(S, min(tj * kTM + kTM - 1, q - 1));
-    const int rmin = block_of(S, ti * kTM), rmax = block_of(S, min(ti * kTM + kTM - 1, q - 1));
-    return cmin == 0 || (rmax >= 1 && rmin <= cmax);
-}
-
-__host__ __device__ inline GramShape mx_shape(const Blocks3& S) {
-    const int q = S.q();
-    const int T = (q + kTM - 1) / kTM;
-    GramShape g;
-    g.ntA = 0;
-    for (int ti = 0; ti < T; ++ti)
-        for (int tj = 0; tj < T; ++tj) g.ntA += mx_a_needed(S, q, ti, tj);
-    g.ntB = T * (T + 1) / 2;
-    const int nt = g.ntA + g.ntB;
-    g.ks = max(1, min(8, 256 / nt));
-    while (g.ks > 1 && max(3 * 16 * g.ks * (T * kTM + 1) * 4, g.ks * nt * 16 * 8) > 48 * 1024) --g.ks;
-    g.gk = 16 * g.ks;
-    return g;
-}
-
-// Tile order: double-float tiles (the X^T X block of S^T S) first, then the float32 tiles.
-__device__ MxTile mx_tile(const Blocks3& S, int q, int idx) {
-    const int T = (q + kTM - 1) / kTM;
-    const int xt = (S.w[0] + kTM - 1) / kTM;
-    int u = idx;
-    for (int ti = 0; ti < xt; ++ti)
-        for (int tj = ti; tj < xt; ++tj) {
-            if (u == 0) return MxTile{ti, tj, false, true};
-            --u;
-        }
-    for (int ti = 0; ti < T; ++ti)
-        for (int tj = 0; tj < T; ++tj)
-            if (mx_a_needed(S, q, ti, tj)) {
-                if (u == 0) return MxTile{ti, tj, true, false};
-                --u;
-            }
-    for (int ti = 0; ti < T; ++ti)
-        for (int tj = ti; tj < T; ++tj) {
-            if (ti < xt && tj < xt) continue;
-            if (u == 0) return MxTile{ti, tj, false, false};
-            --u;
-        }
-    return MxTile{0, 0, false, false};
-}
-
-// S.p = {Xh, W, P}, T.p = {R, AW, AP}; Xl = low plane of X.
-__global__ void __launch_bounds__(kGramMaxThreads)
-    k_gram_mx(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 Tb, const float* __restrict__ Xl,
-              double* __restrict__ part) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    float* sm = reinterpret_cast<float*>(sm_raw);
-    const int q = S.q();
-    const int T = (q + kTM - 1) / kTM;
-    const GramShape gs = mx_shape(S);
-    const int nt = gs.ntA + gs.ntB;
-    const int ldsm = T * kTM + 1;
-    const int plane = gs.gk * ldsm;
-    float* sS = sm;              // S (X hi)
-    float* sL = sm + plane;      // X lo (columns < w0)
-    float* sT = sm + 2 * plane;  // T
-    const int tile = threadIdx.x % nt;
-    const int grp = threadIdx.x / nt;
-    const bool active = grp < gs.ks;
-    const MxTile mt = mx_tile(S, q, tile);
-    const int ti = mt.ti, tj = mt.tj;
-    const int w0 = S.w[0];
-
-    float st_[kTM][kTM], tot[kTM][kTM], cmp[kTM][kTM];
-#pragma unroll
-    for (int a = 0; a < kTM; ++a)
-#pragma unroll
-        for (int b = 0; b < kTM; ++b) st_[a][b] = tot[a][b] = cmp[a][b] = 0.f;
-
-    const int64_t r0 = blockIdx.x * rows_per_part;
-    const int64_t r1 = min(n, r0 + rows_per_part);
-    const float* rhs = mt.isA ? sT : sS;
-    const int nload = gs.gk * T * kTM;
-    for (int64_t base = r0; base < r1; base += gs.gk) {
-        for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-            const int c = e / gs.gk, k = e - c * gs.gk;
-            const int64_t p = base + k;
-            float vs = 0.f, vl = 0.f, vt = 0.f;
-            if (c < q && p < r1) {
-                vs = load_col<float, float, float>(S, c, p);
-                vt = load_col<float, float, float>(Tb, c, p);
-                if (c < w0) vl = __ldg(Xl + (int64_t)c * S.ld + p);
-            }
-            sS[k * ldsm + c] = vs;
-            sL[k * ldsm + c] = vl;
-            sT[k * ldsm + c] = vt;
-        }
-        __syncthreads();
-        if (active) {
-            if (mt.df) {
-                for (int k = grp; k < gs.gk; k += gs.ks) {
-                    float xh[kTM], xl[kTM], yh[kTM], yl[kTM];
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u) {
-                        xh[u] = sS[k * ldsm + ti * kTM + u];
-                        xl[u] = sL[k * ldsm + ti * kTM + u];
-                        yh[u] = sS[k * ldsm + tj * kTM + u];
-                        yl[u] = sL[k * ldsm + tj * kTM + u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                        for (int v = 0; v < kTM; ++v) {
-                            const float pr = xh[u] * yh[v];
-                            float err = fmaf(xh[u], yh[v], -pr);
-                            err = fmaf(xh[u], yl[v], err);
-                            err = fmaf(xl[u], yh[v], err);
-                            const float t = tot[u][v] + pr;
-                            const float z = t - tot[u][v];
-                            const float d = (tot[u][v] - (t - z)) + (pr - z);
-                            tot[u][v] = t;
-                            cmp[u][v] += d + err;
-                        }
-                }
-            } else {
-                for (int k = grp; k < gs.gk; k += gs.ks) {
-                    float a[kTM], b[kTM];
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u) {
-                        a[u] = sS[k * ldsm + ti * kTM + u];
-                        b[u] = rhs[k * ldsm + tj * kTM + u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                        for (int v = 0; v < kTM; ++v) st_[u][v] = fmaf(a[u], b[v], st_[u][v]);
-                }
-#pragma unroll
-                for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                    for (int v = 0; v < kTM; ++v) {
-                        const float y = st_[u][v] - cmp[u][v];
-                        const float t = tot[u][v] + y;
-                        cmp[u][v] = (t - tot[u][v]) - y;
-                        tot[u][v] = t;
-                        st_[u][v] = 0.f;
-                    }
-            }
-        }
-        __syncthreads();
-    }
-    double res[kTM][kTM];
-#pragma unroll
-    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-        for (int v = 0; v < kTM; ++v)
-            res[u][v] = mt.df ? (double)tot[u][v] + (double)cmp[u][v] : (double)tot[u][v] - (double)cmp[u][v];
-    if (gs.ks > 1) {
-        double* red = reinterpret_cast<double*>(sm_raw);
-        if (active)
-#pragma unroll
-            for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
-        __syncthreads();
-        if (grp == 0) {
-#pragma unroll
-            for (int u = 0; u < kTM; ++u)
-#pragma unroll
-                for (int v = 0; v < kTM; ++v) {
-                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
-                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
-                    res[u][v] = sum;
-                }
-        }
-    }
-    if (grp != 0) return;
-    double* out = part + (int64_t)blockIdx.x * 2 * q * q + (mt.isA ? 0 : (int64_t)q * q);
-#pragma unroll
-    for (int u = 0; u < kTM; ++u)
-#pragma unroll
-        for (int v = 0; v < kTM; ++v) {
-            const int i = ti * kTM + u, j = tj * kTM + v;
-            if (i < q && j < q) out[i + (int64_t)q * j] = res[u][v];
-        }
-}
-
-// gramA / gramB of the mixed form from the partials of k_gram_mx (one warp per pair i <= j).
+// gramA / gramB of the mixed form in residual form (S = [X W P], T = [R AW AP], R = AX - X Lambda)
+// from the partial sums of S^T T (entries (i, j) with column j in X or 1 <= block(i) <= block(j))
+// and S^T S (i <= j): X^T AX = (X^T X) Lambda + X^T R symmetrised,
+// (AX)^T s_j = Lambda X^T s_j + R^T s_j, and the W / P part as in the float64 form.  One warp per
+// pair i <= j.
 __global__ void k_gram_finalize_mx(int q, int nparts, const double* __restrict__ part,
                                    double* __restrict__ gA, double* __restrict__ gB,
                                    const double* __restrict__ lam, Blocks3 W) {
@@ -942,37 +521,13 @@ static void gram_t(int64_t n, const Blocks3& S, const Blocks3* AS, double* part,
     k_gram<T0, T12, C><<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
 }
 
-static void gram_mixed(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
-                       cudaStream_t st) {
-    const int q = S.q();
-    const int T = (q + kTM - 1) / kTM;
-    const GramShape gs = gram_shape(S, AS != nullptr, 16);
-    const int nt = gs.ntA + gs.ntB;
-    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
-    LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
-    const size_t stage = 4 * (size_t)gs.gk * (T * kTM + 1) * sizeof(float);
-    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
-    const size_t smem = std::max(stage, red);
-    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
-    const int64_t rows = ceil_div(n, nparts);
-    Blocks3 A = AS ? *AS : S;
-    k_gram_mixed<<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
-}
-
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st) {
     const bool has12 = S.w[1] + S.w[2] > 0;
     const DType t12 = has12 ? S.t12 : S.t0;
     if (S.t0 == DT_F64 && t12 == DT_F64) gram_t<double, double, double>(n, S, AS, part, nparts, st);
-    else if (S.t0 == DT_F64 && t12 == DT_F32) gram_mixed(n, S, AS, part, nparts, st);
     else if (S.t0 == DT_F32 && t12 == DT_F32) gram_t<float, float, float>(n, S, AS, part, nparts, st);
     else throw Error(LOBPCG_ERR_ARG, "unsupported Gram block types");
-    LG_CHECK_LAUNCH();
-}
-
-void launch_gram_f32(int64_t n, const Blocks3& S, double* part, int nparts, cudaStream_t st) {
-    if (S.t0 == DT_F64) gram_t<double, float, float>(n, S, nullptr, part, nparts, st);
-    else gram_t<float, float, float>(n, S, nullptr, part, nparts, st);
     LG_CHECK_LAUNCH();
 }
 
@@ -1025,35 +580,14 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
 }  // namespace lg
 
 namespace lg {
-void launch_project(int64_t n, int b, float* V, const float* S0, int w0, const float* S1, int w1,
-                    int64_t ld, const double* C, int ldc, cudaStream_t st) {
-    if (b <= 0) return;
-    const int groups = (int)ceil_div(b, kCG);
-    const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
-    const size_t smem = (size_t)(w0 + w1) * b * sizeof(float);
-    k_project<<<(unsigned)blocks, dim3(32, groups), smem, st>>>(n, b, V, S0, w0, S1, w1, ld, C, ldc);
-    LG_CHECK_LAUNCH();
-}
-}  // namespace lg
-
-namespace lg {
-void launch_gram_mx(int64_t n, const Blocks3& S, const Blocks3& T, const float* Xl, double* part,
-                    int nparts, const double* lam, double* gramA, double* gramB, cudaStream_t st) {
-    const int q = S.q();
-    const int TT = (q + kTM - 1) / kTM;
-    const GramShape gs = mx_shape(S);
-    const int nt = gs.ntA + gs.ntB;
-    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
-    LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
-    const size_t stage = 3 * (size_t)gs.gk * (TT * kTM + 1) * sizeof(float);
-    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
-    const size_t smem = std::max(stage, red);
-    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
-    const int64_t rows = ceil_div(n, nparts);
-    k_gram_mx<<<nparts, threads, smem, st>>>(n, rows, S, T, Xl, part);
-    LG_CHECK_LAUNCH();
+void launch_gram_finalize_mx(int q, int m, int b, int bp, int nparts, const double* part,
+                             const double* lam, double* gramA, double* gramB, cudaStream_t st) {
+    Blocks3 W{};
+    W.w[0] = m;
+    W.w[1] = b;
+    W.w[2] = bp;
     const int64_t wthreads = (int64_t)q * (q + 1) / 2 * 32;
-    k_gram_finalize_mx<<<(unsigned)ceil_div(wthreads, 256), 256, 0, st>>>(q, nparts, part, gramA, gramB, lam, S);
+    k_gram_finalize_mx<<<(unsigned)ceil_div(wthreads, 256), 256, 0, st>>>(q, nparts, part, gramA, gramB, lam, W);
     LG_CHECK_LAUNCH();
 }
 }  // namespace lg

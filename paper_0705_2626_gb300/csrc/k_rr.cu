@@ -13,16 +13,20 @@
 //                  E_ij = (s_ij + l_j r_ij) / (l_j - l_i) for separated pairs whose correction
 //                  is small (|E_ij| <= 1e-4), r_ij / 2 otherwise, V <- V + V E (each step
 //                  squares the error of the refined pairs);
+//      then one orthonormalisation step V <- V (I + (I - V^T V) / 2);
 //   5. one block:  S = V^T M V is diagonal up to rounding except inside near-degenerate clusters;
 //                  float64 cyclic Jacobi sweeps that rotate only the pairs above 8 eps ||S||_F
 //                  finish it, then C = D Linv^T V Q for the m smallest, ascending.
 // Breakdown rule as elsewhere: a pivot of the unit-diagonal matrix at or below order * 2^-52.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace lg {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
+constexpr int kSubMax = 48;    // largest cleanup submatrix kept beside S and Q in shared memory
 
 // work layout (doubles), all q x q matrices column-major with leading dimension q
 struct RRWork {
@@ -37,17 +41,22 @@ struct RRWork {
 __device__ __forceinline__ int nq_of(const RRWork& w) { return (int)w.hdr[0]; }
 
 // ---------------------------------------------------------------- 1. Cholesky of gramB
-__device__ bool chol_lower_rm(int nq, double* S, int lds, int* flag) {   // row-major, in place
+__device__ bool chol_lower_rm(int nq, double* S, int lds, int* flag, double* rinv) {   // row-major, in place
     for (int k = 0; k < nq; ++k) {
         if (threadIdx.x == 0) {
             const double piv = S[k * lds + k];
-            if (!(piv > nq * kEps) || !isfinite(piv)) *flag = 1;
-            else S[k * lds + k] = sqrt(piv);
+            if (!(piv > nq * kEps) || !isfinite(piv)) {
+                *flag = 1;
+            } else {
+                const double l = sqrt(piv);
+                S[k * lds + k] = l;
+                *rinv = 1.0 / l;    // one division per pivot; the column is scaled by multiplication
+            }
         }
         __syncthreads();
         if (*flag) return false;
-        const double lkk = S[k * lds + k];
-        for (int i = k + 1 + threadIdx.x; i < nq; i += blockDim.x) S[i * lds + k] /= lkk;
+        const double inv = *rinv;
+        for (int i = k + 1 + threadIdx.x; i < nq; i += blockDim.x) S[i * lds + k] *= inv;
         __syncthreads();
         const int rem = nq - k - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
@@ -61,8 +70,10 @@ __device__ bool chol_lower_rm(int nq, double* S, int lds, int* flag) {   // row-
 
 // Linv (row-major in smem) by column-parallel forward substitution: warp w owns columns
 // w, w + nwarps, ...; lane l owns rows l, l + 32, l + 64.
-__device__ void lower_inv(int nq, const double* L, int ldl, double* Li, int ldi) {
+__device__ void lower_inv(int nq, const double* L, int ldl, double* Li, int ldi, double* dinv) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) dinv[k] = 1.0 / L[k * ldl + k];
+    __syncthreads();
     for (int j = wid; j < nq; j += nw) {
         double x[3];
 #pragma unroll
@@ -72,7 +83,7 @@ __device__ void lower_inv(int nq, const double* L, int ldl, double* Li, int ldi)
             double xk = 0.0;
 #pragma unroll
             for (int r = 0; r < 3; ++r)
-                if (r == rk && lane == ok) { x[r] = x[r] / L[k * ldl + k]; xk = x[r]; }
+                if (r == rk && lane == ok) { x[r] = x[r] * dinv[k]; xk = x[r]; }
             xk = __shfl_sync(0xffffffffu, xk, ok);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -93,6 +104,7 @@ __global__ void __launch_bounds__(1024)
               unsigned* status, unsigned skip) {
     extern __shared__ double sm[];
     __shared__ int flag;
+    __shared__ double rinv, dinv[kMaxQ];
     if (*status & skip) return;
     RRWork w(work, q);
     const int ld = q + 1;
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(1024)
                 Lsm[i * ld + j] = w.d[i] * g * w.d[j];
             }
             __syncthreads();
-            chol_lower_rm(nq, Lsm, ld, &flag);
+            chol_lower_rm(nq, Lsm, ld, &flag, &rinv);
         }
         __syncthreads();
         if (!flag) break;
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(1024)
         if (tid == 0) atomicOr(status, (unsigned)ST_RR_BREAKDOWN);
         return;
     }
-    lower_inv(nq, Lsm, ld, Lism, ld);
+    lower_inv(nq, Lsm, ld, Lism, ld, dinv);
     __syncthreads();
     for (int e = tid; e < q * q; e += blockDim.x) {    // Linv column-major, zero outside nq
         const int i = e % q, j = e / q;
@@ -165,75 +177,91 @@ __global__ void k_rr_form_m(int q, const double* __restrict__ gA, double* work, 
 
 // ---------------------------------------------------------------- Jacobi sweeps (shared code)
 // Cyclic Jacobi on the nq x nq symmetric matrix A (row-major, leading dim lda, in shared
-// memory) accumulating the rotations into V (row-major, ldv).  Rotates a pair while
-// |A_pr| > thr.  Returns after a sweep without rotations or after max_sweeps.
+// memory) accumulating the rotations into V (row-major, ldv).  Parallel ordering: the circle
+// method of round-robin tournaments (Golub & Van Loan Sec. 8.5): in round t the index sets
+// {pos(k, t), pos(qe-1-k, t)} with pos(0, t) = 0 and pos(i, t) = 1 + (i - 1 + t) mod (qe - 1)
+// are disjoint pairs, and over qe - 1 rounds every pair meets once.  A pair is rotated while
+// |A_pr| > thr.  Because the pairs of a round are disjoint, J^T A J splits into independent
+// 2 x 2 blocks (pair k rows, pair l columns), so a round is: rotation parameters (one thread
+// per pair), barrier, every 2 x 2 block and every row of V updated in place, barrier.
+// Returns after a sweep without rotations or after max_sweeps.
+__device__ __forceinline__ int rr_pos(int i, int t, int qe) { return i == 0 ? 0 : 1 + (i - 1 + t) % (qe - 1); }
+
 template <typename T>
-__device__ void jacobi_sweeps(int nq, T* A, int lda, T* V, int ldv, T thr, int max_sweeps,
-                              T* rc, T* rs, int* rp, int* rr, int* ord, int* rotated) {
-    const int tid = threadIdx.x;
+__device__ void jacobi_sweeps(int nq, T* A, int lda, T* V, int ldv, T thr, int max_sweeps, T* rc, T* rs,
+                              int* rp, int* rr, int* rotated) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int qe = nq + (nq & 1);
-    const int npairs = qe / 2;
-    for (int i = tid; i < qe; i += blockDim.x) ord[i] = i;
+    const int np = qe / 2;
+    if (qe < 2) return;
+    // *rotated holds 1 + the last sweep that rotated (no reset between barriers needed)
+    if (tid == 0) *rotated = 0;
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (tid == 0) *rotated = 0;
-        __syncthreads();
-        for (int step = 0; step < qe - 1; ++step) {
-            if (tid < npairs) {
-                int p = ord[tid], r = ord[qe - 1 - tid];
-                if (p > r) { const int t = p; p = r; r = t; }
+        for (int t = 0; t < qe - 1; ++t) {
+            if (tid < np) {
+                int p = rr_pos(tid, t, qe), r = rr_pos(qe - 1 - tid, t, qe);
+                if (p > r) { const int x = p; p = r; r = x; }
                 T c = 1, s = 0;
                 if (r < nq) {
-                    const T apq = A[p * lda + r], app = A[p * lda + p], arr = A[r * lda + r];
+                    const T apq = A[p * lda + r];
                     if (fabs(apq) > thr) {
+                        const T app = A[p * lda + p], arr = A[r * lda + r];
                         const T tau = (arr - app) / (T(2) * apq);
-                        const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(fma(tau, tau, T(1))));
-                        c = T(1) / sqrt(fma(t, t, T(1)));
-                        s = t * c;
-                        *rotated = 1;
+                        const T tt = copysign(T(1), tau) / (fabs(tau) + sqrt(fma(tau, tau, T(1))));
+                        c = T(1) / sqrt(fma(tt, tt, T(1)));
+                        s = tt * c;
+                        *rotated = sweep + 1;
                     }
                 }
                 rc[tid] = c; rs[tid] = s; rp[tid] = p; rr[tid] = r;
             }
             __syncthreads();
-            for (int e = tid; e < npairs * nq; e += blockDim.x) {       // rows: A <- J^T A
-                const int k = e / nq, j = e % nq;
-                const T s = rs[k];
-                if (s == T(0)) continue;
-                const T c = rc[k];
-                const int p = rp[k], r = rr[k];
-                const T ap = A[p * lda + j], ar = A[r * lda + j];
-                A[p * lda + j] = c * ap - s * ar;
-                A[r * lda + j] = fma(s, ap, c * ar);
+            // 2 x 2 blocks (pair k rows, pair l columns): rows then columns rotated
+            for (int k = wid; k < np; k += nw) {
+                const T ck = rc[k], sk = rs[k];
+                const int pk = rp[k], rk = rr[k];
+                const bool vk = rk < nq;
+                for (int l = lane; l < np; l += 32) {
+                    const T sl = rs[l];
+                    if (sk == T(0) && sl == T(0)) continue;
+                    const T cl = rc[l];
+                    const int pl = rp[l], rl = rr[l];
+                    const bool vl = rl < nq;
+                    const T a = A[pk * lda + pl];
+                    const T b = vl ? A[pk * lda + rl] : T(0);
+                    const T c0 = vk ? A[rk * lda + pl] : T(0);
+                    const T d = (vk && vl) ? A[rk * lda + rl] : T(0);
+                    const T a1 = ck * a - sk * c0, b1 = ck * b - sk * d;
+                    const T c1 = fma(sk, a, ck * c0), d1 = fma(sk, b, ck * d);
+                    T a2 = cl * a1 - sl * b1, b2 = fma(sl, a1, cl * b1);
+                    T c2 = cl * c1 - sl * d1;
+                    const T d2 = fma(sl, c1, cl * d1);
+                    if (k == l && sk != T(0)) { b2 = T(0); c2 = T(0); }   // the annihilated pair
+                    A[pk * lda + pl] = a2;
+                    if (vl) A[pk * lda + rl] = b2;
+                    if (vk) A[rk * lda + pl] = c2;
+                    if (vk && vl) A[rk * lda + rl] = d2;
+                }
             }
-            __syncthreads();
-            for (int e = tid; e < npairs * nq; e += blockDim.x) {       // columns: A <- A J, V <- V J
-                const int k = e / nq, i = e % nq;
-                const T s = rs[k];
-                if (s == T(0)) continue;
-                const T c = rc[k];
-                const int p = rp[k], r = rr[k];
-                const T ap = A[i * lda + p], ar = A[i * lda + r];
-                A[i * lda + p] = c * ap - s * ar;
-                A[i * lda + r] = fma(s, ap, c * ar);
-                const T vp = V[i * ldv + p], vr = V[i * ldv + r];
-                V[i * ldv + p] = c * vp - s * vr;
-                V[i * ldv + r] = fma(s, vp, c * vr);
-            }
-            __syncthreads();
-            if (tid < npairs && rs[tid] != T(0)) {
-                A[rp[tid] * lda + rr[tid]] = T(0);
-                A[rr[tid] * lda + rp[tid]] = T(0);
-            }
-            if (tid == 0) {
-                const int last = ord[qe - 1];
-                for (int i = qe - 1; i > 1; --i) ord[i] = ord[i - 1];
-                ord[1] = last;
+            // V <- V J: pair k columns of every row
+            for (int k = wid; k < np; k += nw) {
+                const T sk = rs[k];
+                if (sk == T(0)) continue;
+                const T ck = rc[k];
+                const int pk = rp[k], rk = rr[k];
+                for (int i = lane; i < nq; i += 32) {
+                    const T vp = V[i * ldv + pk], vr = V[i * ldv + rk];
+                    V[i * ldv + pk] = ck * vp - sk * vr;
+                    V[i * ldv + rk] = fma(sk, vp, ck * vr);
+                }
             }
             __syncthreads();
         }
-        if (!*rotated) break;
+        // every thread reads the flag before any thread can start the next sweep and write it
+        const bool again = (*rotated == sweep + 1);
         __syncthreads();
+        if (!again) break;
     }
 }
 
@@ -258,7 +286,7 @@ __global__ void __launch_bounds__(1024)
     k_rr_jacobi32(int q, double* work, const unsigned* status, unsigned skip) {
     extern __shared__ float smf[];
     __shared__ float rc[kMaxQ / 2 + 1], rs[kMaxQ / 2 + 1], red[32];
-    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], ord[kMaxQ + 1], rotated;
+    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], rotated;
     if (*status & skip) return;
     RRWork w(work, q);
     const int nq = nq_of(w);
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(1024)
     const float nrm2 = frob_norm_sq<float>(nq, A, ld, red);
     if (threadIdx.x == 0) w.hdr[1] = 0.0;
     // 8 eps32 ||M||_F: below the float32 rounding noise that every rotation leaves behind
-    jacobi_sweeps<float>(nq, A, ld, V, ld, 8.f * 1.2e-7f * sqrtf(nrm2), 12, rc, rs, rp, rr, ord, &rotated);
+    jacobi_sweeps<float>(nq, A, ld, V, ld, 8.f * 1.2e-7f * sqrtf(nrm2), 12, rc, rs, rp, rr, &rotated);
     __syncthreads();
     for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
         const int i = e % q, j = e / q;
@@ -285,6 +313,7 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------- 4. refinement products
 // mode 0: MV[:, j] = M V[:, j].   mode 1: S[:, j] = V^T MV[:, j] and R[:, j] = e_j - V^T V[:, j].
 // mode 2: S[:, j] = V^T MV[:, j] only.   mode 3: V2[:, j] = V[:, j] + V E[:, j].
+// mode 4: R[:, j] = e_j - V^T V[:, j] only.   mode 5: V2[:, j] = V[:, j] + V R[:, j] / 2.
 __global__ void k_rr_gemm(int q, int mode, double* work, const unsigned* status, unsigned skip) {
     __shared__ double x[kMaxQ], z[kMaxQ];
     if (*status & skip) return;
@@ -292,19 +321,24 @@ __global__ void k_rr_gemm(int q, int mode, double* work, const unsigned* status,
     const int nq = nq_of(w);
     const int j = blockIdx.x;
     if (j >= nq) return;
-    const double* B = mode == 0 ? w.V : (mode == 3 ? w.E : w.MV);
+    const double* B = (mode == 0 || mode == 4) ? w.V : (mode == 3 ? w.E : (mode == 5 ? w.R : w.MV));
+    const double sc = mode == 5 ? 0.5 : 1.0;
     for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-        x[k] = B[k + (int64_t)q * j];
+        x[k] = sc * B[k + (int64_t)q * j];
         if (mode == 1) z[k] = w.V[k + (int64_t)q * j];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-        if (mode == 0 || mode == 3) {                       // (M or V) times x
+        if (mode == 0 || mode == 3 || mode == 5) {          // (M or V) times x
             const double* A = mode == 0 ? w.M : w.V;
             double s = 0.0;
             for (int k = 0; k < nq; ++k) s = fma(A[i + (int64_t)q * k], x[k], s);
             if (mode == 0) w.MV[i + (int64_t)q * j] = s;
             else w.V2[i + (int64_t)q * j] = w.V[i + (int64_t)q * j] + s;
+        } else if (mode == 4) {                             // e_j - V^T v_j
+            double r = 0.0;
+            for (int k = 0; k < nq; ++k) r = fma(w.V[k + (int64_t)q * i], x[k], r);
+            w.R[i + (int64_t)q * j] = (i == j ? 1.0 : 0.0) - r;
         } else {                                            // V^T x (and V^T z)
             double s = 0.0, r = 0.0;
             for (int k = 0; k < nq; ++k) {
@@ -318,12 +352,14 @@ __global__ void k_rr_gemm(int q, int mode, double* work, const unsigned* status,
     }
 }
 
-// E of one refinement step (one block).
-__global__ void __launch_bounds__(1024) k_rr_oa_e(int q, double* work, const unsigned* status, unsigned skip) {
+// E of one refinement step: block j writes column j (every block recomputes the norms).
+__global__ void __launch_bounds__(256) k_rr_oa_e(int q, double* work, const unsigned* status, unsigned skip) {
     __shared__ double lt[kMaxQ];
     if (*status & skip) return;
     RRWork w(work, q);
     const int nq = nq_of(w);
+    const int jcol = blockIdx.x;
+    if (jcol >= nq) return;
     for (int i = threadIdx.x; i < nq; i += blockDim.x)
         lt[i] = w.S[i + (int64_t)q * i] / (1.0 - w.R[i + (int64_t)q * i]);
     __syncthreads();
@@ -351,8 +387,8 @@ __global__ void __launch_bounds__(1024) k_rr_oa_e(int q, double* work, const uns
     // the correction is small both ways (|s_ij + l_j r_ij| <= 1e-4 |gap|, and likewise for ji),
     // so that the next step squares its error; E_ij + E_ji = r_ij keeps V orthonormalising.
     // Other pairs are only orthonormalised (r_ij / 2) and finished by the cleanup sweeps.
-    for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
-        const int i = e % nq, j = e / nq;
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+        const int j = jcol;
         const double r = w.R[i + (int64_t)q * j];
         double ev = 0.5 * r;
         if (i != j) {
@@ -372,7 +408,7 @@ __global__ void __launch_bounds__(1024)
                unsigned* status, unsigned skip) {
     extern __shared__ double sm[];
     __shared__ double rc[kMaxQ / 2 + 1], rs[kMaxQ / 2 + 1], red[32], lsort[kMaxQ];
-    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], ord[kMaxQ + 1], perm[kMaxQ], rotated;
+    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], perm[kMaxQ], rotated, act[kMaxQ], idx[kMaxQ], nact;
     if (*status & skip) return;
     RRWork w(work, q);
     const int nq = nq_of(w);
@@ -386,7 +422,46 @@ __global__ void __launch_bounds__(1024)
     }
     __syncthreads();
     const double nrm2 = frob_norm_sq<double>(nq, A, ld, red);
-    jacobi_sweeps<double>(nq, A, ld, Q, ld, 8.0 * kEps * sqrt(nrm2), 8, rc, rs, rp, rr, ord, &rotated);
+    const double thr = 8.0 * kEps * sqrt(nrm2);
+    // After the refinement only the pairs inside near-degenerate clusters stay above thr; the
+    // cleanup runs on the submatrix of those indices (their couplings to the rest are below thr,
+    // so leaving them out changes eigenvalues and vectors only at the rounding level).
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) act[i] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
+        const int i = e / nq, j = e % nq;
+        if (i != j && fabs(A[i * ld + j]) > thr) act[i] = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int i = 0; i < nq; ++i)
+            if (act[i]) idx[na++] = i;
+        nact = na;
+    }
+    __syncthreads();
+    const int na = nact;
+    if (na > kSubMax) {
+        // many unresolved pairs (the refinement did not converge): sweep the whole matrix
+        jacobi_sweeps<double>(nq, A, ld, Q, ld, thr, 16, rc, rs, rp, rr, &rotated);
+    } else if (na >= 2) {
+        const int lds = na + 1;
+        double* As = Q + nq * ld;          // na x na submatrix and its rotations
+        double* Qs = As + na * lds;
+        for (int e = threadIdx.x; e < na * na; e += blockDim.x) {
+            const int a = e / na, b = e % na;
+            As[a * lds + b] = A[idx[a] * ld + idx[b]];
+            Qs[a * lds + b] = (a == b) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        jacobi_sweeps<double>(na, As, lds, Qs, lds, thr, 16, rc, rs, rp, rr, &rotated);
+        __syncthreads();
+        for (int e = threadIdx.x; e < na * na; e += blockDim.x) {
+            const int a = e / na, b = e % na;
+            Q[idx[a] * ld + idx[b]] = Qs[a * lds + b];
+            if (a == b) A[idx[a] * ld + idx[a]] = As[a * lds + a];
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < nq; i += blockDim.x) {
         const double li = A[i * ld + i];
@@ -441,9 +516,10 @@ void launch_rayleigh_ritz(int q, int q_min, int m, const double* gramA, const do
     int dev = 0;
     LG_CUDA(cudaGetDevice(&dev));
     const size_t big64 = 2 * (size_t)kMaxQ * (kMaxQ + 1) * sizeof(double);
+    const size_t fin64 = big64 + 2 * (size_t)kSubMax * (kSubMax + 1) * sizeof(double);
     if (dev < 64 && !attr[dev]) {
         set_smem((const void*)k_rr_chol, big64);
-        set_smem((const void*)k_rr_final, big64);
+        set_smem((const void*)k_rr_final, fin64);
         set_smem((const void*)k_rr_jacobi32, 2 * (size_t)kMaxQ * (kMaxQ + 1) * sizeof(float));
         attr[dev] = true;
     }
@@ -461,18 +537,28 @@ void launch_rayleigh_ritz(int q, int q_min, int m, const double* gramA, const do
         LG_CHECK_LAUNCH();
         k_rr_gemm<<<q, 128, 0, st>>>(q, 1, work, status, skip);   // S, R
         LG_CHECK_LAUNCH();
-        k_rr_oa_e<<<1, 1024, 0, st>>>(q, work, status, skip);
+        k_rr_oa_e<<<q, 256, 0, st>>>(q, work, status, skip);
         LG_CHECK_LAUNCH();
         k_rr_gemm<<<q, 128, 0, st>>>(q, 3, work, status, skip);   // V2 = V + V E
         LG_CHECK_LAUNCH();
         LG_CUDA(cudaMemcpyAsync(work + 2 * (size_t)q * q, work + 3 * (size_t)q * q,
                                 (size_t)q * q * sizeof(double), cudaMemcpyDeviceToDevice, st));   // V = V2
     }
+    // one more orthonormalisation step, V <- V (I + R / 2): the refinement steps leave V
+    // orthonormal only to the square of their largest correction, and S below must be an exact
+    // similarity transform of M for the cleanup to give eigenvectors of M
+    k_rr_gemm<<<q, 128, 0, st>>>(q, 4, work, status, skip);       // R = I - V^T V
+    LG_CHECK_LAUNCH();
+    k_rr_gemm<<<q, 128, 0, st>>>(q, 5, work, status, skip);       // V2 = V + V R / 2
+    LG_CHECK_LAUNCH();
+    LG_CUDA(cudaMemcpyAsync(work + 2 * (size_t)q * q, work + 3 * (size_t)q * q, (size_t)q * q * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st));    // V = V2
     k_rr_gemm<<<q, 128, 0, st>>>(q, 0, work, status, skip);       // MV = M V
     LG_CHECK_LAUNCH();
     k_rr_gemm<<<q, 128, 0, st>>>(q, 2, work, status, skip);       // S = V^T M V
     LG_CHECK_LAUNCH();
-    k_rr_final<<<1, 1024, s64, st>>>(q, m, work, lam, C, status, skip);
+    const size_t sfin = s64 + 2 * (size_t)std::min(q, kSubMax) * (std::min(q, kSubMax) + 1) * sizeof(double);
+    k_rr_final<<<1, 1024, sfin, st>>>(q, m, work, lam, C, status, skip);
     LG_CHECK_LAUNCH();
 }
 

@@ -17,6 +17,9 @@
 // point) and float32 otherwise (bound by HBM).
 #include <cuda_bf16.h>
 
+#include <cstdint>
+#include <type_traits>
+
 #include "common.cuh"
 #include "dtype.cuh"
 
@@ -76,6 +79,64 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
 }
 
+// Float32 storage with nx divisible by 4: each thread owns 4 consecutive points of an x-row
+// (one float4) and marches along k, so a point costs about 1.25 load instructions instead of 6.
+// Same arithmetic as the float32 branch above (difference form, neighbours added in the same
+// order).
+template <bool HAS_Z>
+__global__ void __launch_bounds__(kTX* kTY)
+    k_stencil_f32v4(Grid3 g, int zchunk, int nzc, float a, float b, const float* __restrict__ x, int64_t ldx,
+                    float c, const float* __restrict__ z, int64_t ldz, float* __restrict__ y, int64_t ldy) {
+    const int nx4 = g.nx >> 2;
+    const int i4 = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / nzc;
+    const int kc = blockIdx.z - col * nzc;
+    if (i4 >= nx4 || j >= g.ny) return;
+    const int i0 = 4 * i4;
+    const int k0 = kc * zchunk;
+    const int k1 = min(k0 + zchunk, g.nz);
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const float* xc = x + (int64_t)col * ldx;
+    const float* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
+    float* yc = y + (int64_t)col * ldy;
+    auto ld4 = [](const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); };
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t p = i0 + sy * (j + (int64_t)g.ny * k0);
+    float4 xm = k0 > 0 ? ld4(xc + p - sz) : zero;
+    float4 x0 = ld4(xc + p);
+    const bool hasl = i0 > 0, hasr = i0 + 4 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
+    const float a6 = a + 6.f * b;
+    for (int k = k0; k < k1; ++k, p += sz) {
+        const float4 xp = (k + 1 < g.nz) ? ld4(xc + p + sz) : zero;
+        const float l = hasl ? __ldg(xc + p - 1) : 0.f;
+        const float r = hasr ? __ldg(xc + p + 4) : 0.f;
+        const float4 yd = hasd ? ld4(xc + p - sy) : zero;
+        const float4 yu = hasu ? ld4(xc + p + sy) : zero;
+        const float4 zz = HAS_Z ? ld4(zc + p) : zero;
+        const float cx[6] = {l, x0.x, x0.y, x0.z, x0.w, r};
+        const float m_[4] = {xm.x, xm.y, xm.z, xm.w}, p_[4] = {xp.x, xp.y, xp.z, xp.w};
+        const float d_[4] = {yd.x, yd.y, yd.z, yd.w}, u_[4] = {yu.x, yu.y, yu.z, yu.w};
+        const float z_[4] = {zz.x, zz.y, zz.z, zz.w};
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float xv = cx[e + 1];
+            float d = (xv - m_[e]) + (xv - p_[e]);
+            d += xv - cx[e];
+            d += xv - cx[e + 2];
+            d += xv - d_[e];
+            d += xv - u_[e];
+            float v = fmaf(-b, d, a6 * xv);
+            if (HAS_Z) v = fmaf(c, z_[e], v);
+            o[e] = v;
+        }
+        *reinterpret_cast<float4*>(yc + p) = make_float4(o[0], o[1], o[2], o[3]);
+        xm = x0;
+        x0 = xp;
+    }
+}
+
 // Full weighting: coarse point (I, J, K) (0-based) sits on fine (2I+1, 2J+1, 2K+1);
 // weights 1, 1/2 per axis for offsets 0, +-1, overall factor 1/8 (R = P^T / 8).
 template <typename TF, typename TC>
@@ -111,53 +172,74 @@ __global__ void __launch_bounds__(kTX* kTY)
     st_as(rc + (int64_t)col * ldc + I + (int64_t)gc.nx * (J + (int64_t)gc.ny * K), C(0.125) * s);
 }
 
-// Trilinear prolongation: fine index f (1-based) takes coarse f/2 with weight 1 when f is
-// even, coarse (f-1)/2 and (f+1)/2 with weight 1/2 each when f is odd; coarse indices 0
-// and nc+1 are boundary zeros.  Per axis: two taps (index, weight), weight 0 when absent.
-__device__ __forceinline__ void taps1d(int f0, int nc, int& i0, int& i1, float& w0, float& w1) {
-    const int f = f0 + 1;
-    if ((f & 1) == 0) {
-        const int I = f >> 1;
-        i0 = I - 1; w0 = I <= nc ? 1.0f : 0.0f;
-        i1 = i0;    w1 = 0.0f;
-    } else {
-        const int I1 = (f - 1) >> 1, I2 = (f + 1) >> 1;
-        i0 = I1 - 1; w0 = I1 >= 1 ? 0.5f : 0.0f;
-        i1 = I2 - 1; w1 = I2 <= nc ? 0.5f : 0.0f;
-    }
-    i0 = max(0, min(i0, nc - 1));   // clamp: a zero-weight tap still reads in bounds
-    i1 = max(0, min(i1, nc - 1));
-}
-
+// Prolongation by coarse cells: cell (Cx, Cy, Cz), 0 <= C <= nc per axis, lies between the
+// coarse points C and C+1 (1-based; 0 and nc+1 are the zero boundary) and owns the fine points
+// 2C+1 (midpoint, weight 1/2 each) and 2C+2 (on coarse C+1, weight 1) of each axis that exist.
+// A thread owns a (Cx, Cy) column of cells and marches along Cz carrying the lower coarse plane,
+// so each coarse value is loaded about once per 8 fine points it feeds.
 template <typename TC, typename TF>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_prolong_add(Grid3 gf, Grid3 gc, const TC* __restrict__ ec, int64_t ldc, TF* __restrict__ ef,
-                  int64_t ldf) {
+    k_prolong_add(Grid3 gf, Grid3 gc, int zchunk, int nzc, const TC* __restrict__ ec, int64_t ldc,
+                  TF* __restrict__ ef, int64_t ldf) {
     using C = typename Acc<TF>::type;
-    const int i = blockIdx.x * kTX + threadIdx.x;
-    const int j = blockIdx.y * kTY + threadIdx.y;
-    const int col = blockIdx.z / gf.nz;
-    const int k = blockIdx.z - col * gf.nz;
-    if (i >= gf.nx || j >= gf.ny) return;
+    const int cx = blockIdx.x * kTX + threadIdx.x;
+    const int cy = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / nzc;
+    const int kc = blockIdx.z - col * nzc;
+    if (cx > gc.nx || cy > gc.ny) return;
+    const int z0 = kc * zchunk;
+    const int z1 = min(z0 + zchunk, gc.nz + 1);
     const TC* c = ec + (int64_t)col * ldc;
-    int xi[2], yi[2], zi[2];
-    float xw[2], yw[2], zw[2];
-    taps1d(i, gc.nx, xi[0], xi[1], xw[0], xw[1]);
-    taps1d(j, gc.ny, yi[0], yi[1], yw[0], yw[1]);
-    taps1d(k, gc.nz, zi[0], zi[1], zw[0], zw[1]);
-    C s = 0;
+    TF* f = ef + (int64_t)col * ldf;
+    const int64_t csy = gc.nx, csz = (int64_t)gc.nx * gc.ny;
+    const int64_t fsy = gf.nx, fsz = (int64_t)gf.nx * gf.ny;
+    // coarse value at 1-based (X, Y, Z), zero outside 1..nc
+    auto cv = [&](int X, int Y, int Z) -> C {
+        if (X < 1 || X > gc.nx || Y < 1 || Y > gc.ny || Z < 1 || Z > gc.nz) return C(0);
+        return C(ld_as(c + (X - 1) + csy * (Y - 1) + csz * (Z - 1)));
+    };
+    // lo[b][a]: plane Z = Cz, hi[b][a]: plane Z = Cz + 1; a, b select X = cx + a, Y = cy + b
+    C lo[2][2], hi[2][2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const C w = C(zw[a]) * C(yw[b]);
-            const int64_t row = (int64_t)gc.nx * (yi[b] + (int64_t)gc.ny * zi[a]);
+        for (int a = 0; a < 2; ++a) lo[b][a] = cv(cx + a, cy + b, z0);
+    for (int cz = z0; cz < z1; ++cz) {
 #pragma unroll
-            for (int d = 0; d < 2; ++d) s = fma(w * C(xw[d]), C(ld_as(c + row + xi[d])), s);
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) hi[b][a] = cv(cx + a, cy + b, cz + 1);
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+            const int fz = 2 * cz + dz;           // 0-based fine index
+            if (fz >= gf.nz) break;
+            C pz[2][2];
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) pz[b][a] = dz ? hi[b][a] : C(0.5) * (lo[b][a] + hi[b][a]);
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int fy = 2 * cy + dy;
+                if (fy >= gf.ny) break;
+                const C py0 = dy ? pz[1][0] : C(0.5) * (pz[0][0] + pz[1][0]);
+                const C py1 = dy ? pz[1][1] : C(0.5) * (pz[0][1] + pz[1][1]);
+                const int64_t row = fsy * fy + fsz * fz;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int fx = 2 * cx + dx;
+                    if (fx >= gf.nx) break;
+                    const C v = dx ? py1 : C(0.5) * (py0 + py1);
+                    TF* q = f + row + fx;
+                    st_as(q, C(ld_as(q)) + v);
+                }
+            }
         }
-    const int64_t p = (int64_t)col * ldf + i + (int64_t)gf.nx * (j + (int64_t)gf.ny * k);
-    const C old = ld_as(ef + p);
-    st_as(ef + p, old + s);
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) lo[b][a] = hi[b][a];
+    }
 }
 
 // Coarsest-level exact solve.  The 7-point Dirichlet operator s*(6u - nb) on an
@@ -251,8 +333,21 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
     using C = typename Acc<T>::type;
     const int zc = zchunk_for(g.nz);
     const int nzc = (int)ceil_div(g.nz, zc);
-    dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
     dim3 block(kTX, kTY);
+    if constexpr (std::is_same<T, float>::value) {
+        if (g.nx % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && (!z || ldz % 4 == 0) &&
+            ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % 16 == 0) {
+            dim3 grid4((unsigned)ceil_div(g.nx / 4, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
+            if (z)
+                k_stencil_f32v4<true><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const float*)x, ldx,
+                                                               (float)c, (const float*)z, ldz, (float*)y, ldy);
+            else
+                k_stencil_f32v4<false><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const float*)x, ldx,
+                                                                0.f, nullptr, 0, (float*)y, ldy);
+            return;
+        }
+    }
+    dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
     if (z)
         k_stencil_axpby<T, true><<<grid, block, 0, st>>>(g, zc, nzc, (C)a, (C)b, (const T*)x, ldx, (C)c,
                                                          (const T*)z, ldz, (T*)y, ldy);
@@ -269,10 +364,12 @@ void restrict_t(const Grid3& gf, const Grid3& gc, int ncols, const void* rf, int
 }
 
 template <typename TC, typename TF>
-void prolong_t(const Grid3& gf, const Grid3& gc, int ncols, const void* ec, int64_t ldc, void* ef,
-               int64_t ldf, cudaStream_t st) {
-    dim3 grid((unsigned)ceil_div(gf.nx, kTX), (unsigned)ceil_div(gf.ny, kTY), (unsigned)(gf.nz * ncols));
-    k_prolong_add<TC, TF><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, (const TC*)ec, ldc, (TF*)ef, ldf);
+void prolong_t(const Grid3& gf, const Grid3& gc, int ncols, const void* ec, int64_t ldc, void* ef, int64_t ldf,
+               cudaStream_t st) {
+    const int zc = zchunk_for(gc.nz + 1);
+    const int nzc = (int)ceil_div(gc.nz + 1, zc);
+    dim3 grid((unsigned)ceil_div(gc.nx + 1, kTX), (unsigned)ceil_div(gc.ny + 1, kTY), (unsigned)(nzc * ncols));
+    k_prolong_add<TC, TF><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, zc, nzc, (const TC*)ec, ldc, (TF*)ef, ldf);
 }
 
 template <typename TS, typename TD>

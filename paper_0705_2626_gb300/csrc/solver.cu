@@ -38,7 +38,11 @@ struct Buf {
 };
 inline double* f64(const Buf& b) { return static_cast<double*>(b.p); }
 
-constexpr int kMaxFp64Sweeps = 8;
+constexpr int kMaxFp64Sweeps = 16;
+// Mixed form: the loop drops a column at kMixedInnerTol * tol, so that the float64 sweep, which
+// re-orthonormalises X and rotates it within clusters of close Ritz values, still finds every
+// column below tol instead of pushing the ones that passed with no margin back over it.
+constexpr double kMixedInnerTol = 0.5;
 
 }  // namespace
 
@@ -95,6 +99,7 @@ struct lobpcg_handle {
     std::vector<int> J;
     std::vector<double> lam_h, norms_h, resid_h;
     std::vector<int> norm_cols;                 // columns whose norms the last residual pass computed
+    bool norms_fp64 = true;                     // mixed form: last norms from the float64 sweep
     std::vector<double> norm_by_col;            // those norms, indexed by column
     int p_dropped = 0;
     int fp64_sweeps = 0;
@@ -182,8 +187,9 @@ void ensure_workspace(lobpcg_t* h, int wm) {
         ensure(h, h->lt[l], bytes);
     }
     const int q = 3 * wm;
-    h->part_doubles = (size_t)std::max<int64_t>(gram_scratch_doubles(n, q),
-                                                (int64_t)residual_chunks(n) * wm);
+    h->part_doubles = (size_t)std::max<int64_t>(
+        std::max<int64_t>(gram_scratch_doubles(n, q), (int64_t)g32_chunks(n) * 2 * q * q),
+        std::max<int64_t>(residual_chunks(n), resid_mx_blocks(h->g)) * wm);
     ensure(h, h->part, h->part_doubles * sizeof(double));
     const size_t nsmall = 2 * (size_t)q * q + (size_t)q * wm + wm + (size_t)wm * wm + wm +
                           (size_t)rr_work_doubles(q) + (size_t)wm * wm + 8;
@@ -317,15 +323,33 @@ void project_out(lobpcg_t* h, int b, void* V, const void* W) {
     const int64_t n = h->g.n();
     const int m = h->m;
     const int wb = W ? b : 0;
-    const int q = m + wb + b;
-    const int nparts = gram_parts(n);
+    const float* Xh = static_cast<const float*>(h->Xh.p);
+    const float* Wf = static_cast<const float*>(W);
     for (int pass = 0; pass < 2; ++pass) {
-        const Blocks3 S = blocks(h->Xh.p, m, DT_F32, W ? W : V, b, V, W ? b : 0, DT_F32, h->ld);
-        launch_gram_f32(n, S, f64(h->part), nparts, h->stream);
-        launch_gram_finalize(q, nparts, f64(h->part), false, nullptr, h->gramB, nullptr, &S, h->stream);
-        // coefficients: rows 0 .. m + wb - 1 of the last b columns of gramB
-        launch_project(n, b, static_cast<float*>(V), static_cast<const float*>(h->Xh.p), m,
-                       static_cast<const float*>(W), wb, h->ld, h->gramB + (size_t)(m + wb) * q, q, h->stream);
+        // coefficients [X W]^T V ((m + wb) x b) in gramB, which is free until steps 17-23
+        launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, static_cast<const float*>(V), b, h->gramB, nullptr,
+                            f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+        launch_project32(n, b, static_cast<float*>(V), Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status,
+                         h->stream);
+    }
+}
+
+// V <- V Rinv (steps 11 and 15), in place; skipped on the device if *status & skip.
+void apply_rinv(lobpcg_t* h, int b, DType t, void* V, unsigned skip) {
+    if (t == DT_F32)
+        launch_apply32(h->g.n(), b, static_cast<float*>(V), h->ld, h->Rinv, h->status, skip, h->status, h->stream);
+    else
+        launch_apply_rinv(h->g.n(), b, t, V, h->ld, V, h->ld, h->Rinv, h->status, skip, h->stream);
+}
+
+// G = V^T V for the Cholesky orthonormalisation of a W / P block (steps 11 and 13).
+void block_gram(lobpcg_t* h, int b, DType t, const void* V, double* G) {
+    if (t == DT_F32) {
+        launch_gram32_cross(h->g.n(), h->ld, nullptr, 0, nullptr, 0, static_cast<const float*>(V), b, nullptr, G,
+                            f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+    } else {
+        const Blocks3 S = blocks(V, b, t, nullptr, 0, nullptr, 0, t, h->ld);
+        gram(h, S, nullptr, h->gramA, G, nullptr);
     }
 }
 
@@ -346,6 +370,7 @@ void events_create(lobpcg_t* h) {
 
 // ------------------------------------------------------------------ the iteration
 void residual_into_W(lobpcg_t* h) {
+    h->norms_fp64 = true;
     // step 7: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]] and the norms (to the host).  The
     // mixed form computes the residual R of all m columns (its Gram uses R for every column).
     const int64_t n = h->g.n();
@@ -361,6 +386,24 @@ void residual_into_W(lobpcg_t* h) {
     launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, h->tw, mixed ? h->R.p : h->W.p, h->ld,
                     f64(h->part), h->stream);
     launch_norms_finalize(cols.n, residual_chunks(n), f64(h->part), h->norms, h->stream);
+}
+
+// Mixed form, step 7 from the double-float planes of X: R = A X - X Lambda for all m columns.
+void residual_from_planes(lobpcg_t* h) {
+    const int m = h->m;
+    h->norms_fp64 = false;
+    h->norm_cols.resize(m);
+    for (int j = 0; j < m; ++j) h->norm_cols[j] = j;
+    launch_resid_mx(h->g, m, h->scale, static_cast<const float*>(h->Xh.p), static_cast<const float*>(h->Xl.p),
+                    h->ld, h->lam, static_cast<float*>(h->R.p), h->ld, f64(h->part), h->stream);
+    launch_norms_finalize(m, resid_mx_blocks(h->g), f64(h->part), h->norms, h->stream);
+}
+
+// Mixed form: the float64 copy of X (for the float64 sweep and the results) from the planes.
+void sync_x_from_planes(lobpcg_t* h) {
+    if (h->precision != LOBPCG_MIXED) return;
+    launch_planes_to_f64(h->g.n(), h->m, static_cast<const float*>(h->Xh.p), static_cast<const float*>(h->Xl.p),
+                         h->ld, f64(h->X), h->ld, h->stream);
 }
 
 // Copy the small per-iteration results to the host: norms of J, lambda, status word.
@@ -407,6 +450,7 @@ void orthonormalize_and_rr(lobpcg_t* h) {
 }
 
 void check_setup_status(lobpcg_t* h, unsigned stw) {
+    if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite entry in the block X");
     if (stw & (ST_X_BREAKDOWN | ST_RR_BREAKDOWN))
         throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (step 3)");
@@ -455,17 +499,29 @@ bool check_and_lock(lobpcg_t* h) {
     h->pending_check = false;
     for (double v : h->norms_h)
         if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite residual norm");
+    auto bound_of = [&](int j) {
+        double bound = h->tol_mode == LOBPCG_TOL_RELATIVE ? h->tol * std::fabs(h->lam_h[j]) : h->tol;
+        if (h->precision == LOBPCG_MIXED && !h->norms_fp64) bound *= kMixedInnerTol;
+        return bound;
+    };
+    if (h->precision == LOBPCG_MIXED) {
+        // The mixed form has the residuals of all m columns every pass and re-activates a
+        // soft-locked column whose residual grew again: the Rayleigh-Ritz step keeps rotating
+        // locked columns, and inside a cluster of equal Ritz values it can move the error of an
+        // active column into a locked one.  (The float64 form keeps the paper's rule: J only
+        // shrinks.)
+        std::vector<int> nJ;
+        for (int j = 0; j < h->m; ++j)
+            if (!(h->norm_by_col[j] <= bound_of(j))) nJ.push_back(j);
+        h->J.swap(nJ);
+        return h->J.empty();
+    }
     std::vector<int> keep;   // positions t in the old J that stay active
     for (size_t t = 0; t < h->J.size(); ++t) {
         const int j = h->J[t];
-        const double bound = h->tol_mode == LOBPCG_TOL_RELATIVE ? h->tol * std::fabs(h->lam_h[j]) : h->tol;
-        if (!(h->norm_by_col[j] <= bound)) keep.push_back((int)t);
+        if (!(h->norm_by_col[j] <= bound_of(j))) keep.push_back((int)t);
     }
-    if (keep.size() != h->J.size() && h->precision == LOBPCG_MIXED) {
-        std::vector<int> nJ;
-        for (int t : keep) nJ.push_back(h->J[t]);
-        h->J.swap(nJ);
-    } else if (keep.size() != h->J.size()) {
+    if (keep.size() != h->J.size()) {
         // compact the residual block W to the surviving columns
         std::vector<int> nJ;
         const size_t es = dtype_size(h->tw);
@@ -507,10 +563,9 @@ void pass_body(lobpcg_t* h) {
     if (mixed) project_out(h, b, h->W.p, nullptr);
     tm.mark(1);
     // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
-    const Blocks3 SW = blocks(h->W.p, b, tw, nullptr, 0, nullptr, 0, tw, ld);
-    gram(h, SW, nullptr, h->gramA, h->Gsmall, nullptr);
+    block_gram(h, b, tw, h->W.p, h->Gsmall);
     launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
-    launch_apply_rinv(n, b, tw, h->W.p, ld, h->W.p, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+    apply_rinv(h, b, tw, h->W.p, ST_W_BREAKDOWN);
     tm.mark(2);
     // step 12: AW_J = A W_J
     spmv(h, b, tw, h->W.p, ld, h->AW.p, ld);
@@ -533,10 +588,9 @@ void pass_body(lobpcg_t* h) {
             APj = h->APc.p;
         }
         if (mixed) project_out(h, b, Pj, h->W.p);
-        const Blocks3 SP = blocks(Pj, b, tw, nullptr, 0, nullptr, 0, tw, ld);
-        gram(h, SP, nullptr, h->gramA, h->Gsmall, nullptr);
+        block_gram(h, b, tw, Pj, h->Gsmall);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
-        launch_apply_rinv(n, b, tw, Pj, ld, Pj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+        apply_rinv(h, b, tw, Pj, ST_W_BREAKDOWN | ST_P_DROPPED);
         if (h->precision == LOBPCG_MIXED) {
             // Mixed form: AP_J = A P_J by one more (float32) SpMV.  P_J is nearly rank deficient
             // near convergence, and R^-1 would magnify the separate float32 roundings of P_J and
@@ -552,12 +606,9 @@ void pass_body(lobpcg_t* h) {
     const Blocks3 AS = blocks(h->AX.p, m, DT_F64, h->AW.p, b, APj, use_p ? b : 0, tw, ld);
     const int q = S.q();
     if (mixed) {
-        const Blocks3 SH = blocks(h->Xh.p, m, DT_F32, h->W.p, b, Pj, use_p ? b : 0, DT_F32, ld);
-        const Blocks3 TR = blocks(h->R.p, m, DT_F32, h->AW.p, b, APj, use_p ? b : 0, DT_F32, ld);
-        const int nparts = gram_parts(n);
-        LG_REQUIRE((size_t)nparts * 2 * q * q <= h->part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
-        launch_gram_mx(n, SH, TR, static_cast<const float*>(h->Xl.p), f64(h->part), nparts, h->lam,
-                       h->gramA, h->gramB, st);
+        auto F = [](const void* p) { return static_cast<const float*>(p); };
+        launch_gram_mx2(n, ld, F(h->Xh.p), F(h->Xl.p), F(h->W.p), F(Pj), F(h->R.p), F(h->AW.p), F(APj), m, b,
+                        use_p ? b : 0, f64(h->part), (int64_t)h->part_doubles, h->lam, h->gramA, h->gramB, h->status, st);
     } else {
         gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
     }
@@ -568,19 +619,21 @@ void pass_body(lobpcg_t* h) {
     tm.mark(6);
     // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
     const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
-    launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st,
-                  mixed ? static_cast<float*>(h->Xh.p) : nullptr, mixed ? static_cast<float*>(h->Xl.p) : nullptr);
     if (mixed) {
-        // Mixed form: AX = A X by a float64 SpMV (cheaper than the float64 update AX C_X, and
-        // free of the drift that float32 AP would add to an implicitly updated AX).  AP is
-        // recomputed from P in the next pass.
-        spmv(h, m, DT_F64, h->X.p, ld, h->AX.p, ld);
+        // Mixed form: X as double-float planes; no AX update -- the next residual applies A to X
+        // directly (free of the drift that float32 AP would add to an implicitly updated AX),
+        // and AP is recomputed from P in the next pass.
+        launch_update_mx2(n, m, static_cast<float*>(h->Xh.p), static_cast<float*>(h->Xl.p),
+                          static_cast<const float*>(h->W.p), b, static_cast<const float*>(Pj), use_p ? b : 0, ld,
+                          h->Cm, q, static_cast<float*>(h->P.p), h->status, skip, h->status, st);
     } else {
+        launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st);
         launch_update(n, m, AS, h->Cm, f64(h->AX), h->AP.p, ld, h->status, skip, st);
     }
     tm.mark(7);
     // step 7 of the next pass
-    residual_into_W(h);
+    if (mixed) residual_from_planes(h);
+    else residual_into_W(h);
     const unsigned stw = fetch_small(h);
     if (h->phase_timing) {
         // events 0..7 bracket phases 1..7 of this pass; the residual phase is the tail
@@ -591,6 +644,7 @@ void pass_body(lobpcg_t* h) {
         }
     }
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+    if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (stw & ST_P_DROPPED) ++h->p_dropped;
     if (stw & ST_W_BREAKDOWN)
         throw Error(LOBPCG_ERR_BREAKDOWN, "W_J^T W_J is not numerically positive definite (step 11)");
@@ -605,6 +659,7 @@ void pass_body(lobpcg_t* h) {
 // holds the columns whose float64 residual still fails.
 void fp64_correction(lobpcg_t* h) {
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    sync_x_from_planes(h);
     orthonormalize_and_rr(h);
     const unsigned stw = fetch_small(h);
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
@@ -617,6 +672,7 @@ void fp64_correction(lobpcg_t* h) {
 void finish(lobpcg_t* h) {
     const int64_t n = h->g.n();
     const int m = h->m;
+    sync_x_from_planes(h);
     spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
     ColList cols = identity_cols(m);
     launch_residual(n, cols, f64(h->X), f64(h->AX), h->ld, h->lam, DT_F64, nullptr, 0, f64(h->part),
@@ -1009,6 +1065,50 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
         const Blocks3 AS = blocks(AS0, w0, DT_F64, AS1, w1, AS2, w2, DT_F64, ld);
         gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr);
         LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_gram_f32(lobpcg_t* h, const float* S0, int w0, const float* S1, int w1, const float* V, int b,
+                       int64_t ld, double* C, double* G) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(V && b >= 1 && b <= LOBPCG_MAX_M && w0 >= 0 && w1 >= 0 && w0 + w1 <= 2 * LOBPCG_MAX_M &&
+                       (w0 == 0 || S0) && (w1 == 0 || S1) && valid_ld(ld, n),
+                   LOBPCG_ERR_ARG, "invalid float32 Gram arguments");
+        ensure_workspace(h, std::max(h->wm, (w0 + w1 + b + 2) / 3));
+        cudaStream_t st = h->stream;
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        launch_gram32_cross(n, ld, S0, w0, S1, w1, V, b, (w0 + w1) ? C : nullptr, G, f64(h->part),
+                            (int64_t)h->part_doubles, h->status, st);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        LG_CUDA(cudaStreamSynchronize(st));
+        if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_gram_residual(lobpcg_t* h, const float* Xh, const float* Xl, const float* W, const float* P,
+                            const float* R, const float* AW, const float* AP, int64_t ld, int m, int b, int bp,
+                            const double* lambda, double* gramA, double* gramB) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(Xh && Xl && R && lambda && gramA && gramB && m >= 1 && m <= LOBPCG_MAX_M && b >= 1 &&
+                       b <= LOBPCG_MAX_M && bp >= 0 && bp <= LOBPCG_MAX_M && W && AW && (bp == 0 || (P && AP)) &&
+                       valid_ld(ld, n),
+                   LOBPCG_ERR_ARG, "invalid residual-form Gram arguments");
+        ensure_workspace(h, std::max(h->wm, (m + b + bp + 2) / 3));
+        cudaStream_t st = h->stream;
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+        launch_gram_mx2(n, ld, Xh, Xl, W, bp ? P : W, R, AW, bp ? AP : AW, m, b, bp, f64(h->part),
+                        (int64_t)h->part_doubles, lambda, gramA, gramB, h->status, st);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        LG_CUDA(cudaStreamSynchronize(st));
+        if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
         return LOBPCG_OK;
     });
 }
