@@ -4,9 +4,11 @@
 A step is one LOBPCG iteration (Algorithm steps 7-33 of the BLOPEX paper, Section 2.2: residual,
 V-cycle preconditioner, Cholesky orthonormalisation of W and P, stencil SpMV, Gram matrices,
 Rayleigh-Ritz, Ritz update) over the whole block.  Default workload: the 7-point Dirichlet
-Laplacian on a 128^3 interior grid (2,097,152 unknowns), m = 16 eigenpairs, 6-level V-cycle,
-float64 throughout.  The timed steps run with tol = 0 so that every column stays active (fixed
-work per step); the time to reach tol = 1e-8 is measured separately and reported beside it.
+Laplacian on a 128^3 interior grid (2,097,152 unknowns), m = 16 eigenpairs, 6-level V-cycle.
+The JSON line's value is the float64 form; the mixed form (float32 / bfloat16 blocks, double-float
+X, float64 Rayleigh-Ritz and correction sweep) is timed the same way and reported beside it.  The
+timed steps run with tol = 0 so that every column stays active (fixed work per step); the time to
+reach tol = 1e-8 is measured separately for both forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
 
@@ -39,16 +41,28 @@ WORKLOADS = {
 # FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
+
 # DRAM traffic per launch of the Gram kernel (steps 17-23) from one ncu capture, keyed by the
 # SHA-256 of the kernel source it was taken on; a changed source invalidates it (traffic = null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("c2", "b83558017f53b3e5"): 1.617388e9 + 13.800192e6}
 
 
 def workload_desc(w):
     d = WORKLOADS[w]
     n = d["dims"][0] * d["dims"][1] * d["dims"][2]
     return (f"7-point Dirichlet Laplacian {d['dims'][0]}x{d['dims'][1]}x{d['dims'][2]} ({n:,} unknowns), "
-            f"m={d['m']}, {d['levels']}-level GMG V-cycle (2+2 weighted Jacobi, w=2/3), float64")
+            f"m={d['m']}, {d['levels']}-level GMG V-cycle (2+2 weighted Jacobi, w=2/3); float64 form timed, "
+            f"mixed form beside it")
 
 
 class ClockSampler:
@@ -114,6 +128,36 @@ def kernel_source_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def level_points(dims, levels):
+    out, d = [], tuple(dims)
+    for _ in range(levels):
+        out.append(d[0] * d[1] * d[2])
+        d = tuple(x // 2 for x in d)
+    return out
+
+
+def vcycle_bytes(dims, levels, b, s0, sc):
+    """Compulsory bytes of one V-cycle on b columns as the library runs it: per level above the
+    coarsest, 14 passes over level vectors (fused first two pre-sweeps 2, residual 3, restriction
+    read 1, prolongation read+write 2, two post-sweeps 6) plus the coarse vector written and
+    read once (2 x 1/8); the coarsest level is read and written once.  s0: bytes per value on
+    level 0, sc: on coarser levels."""
+    pts = level_points(dims, levels)
+    total = 0.0
+    for l, n_l in enumerate(pts):
+        s_l = s0 if l == 0 else sc
+        if l == len(pts) - 1:
+            total += n_l * b * 2 * s_l
+        else:
+            total += n_l * b * (14 * s_l + 2 * sc / 8)
+    return total
+
+
+def hbm_frac(nbytes, ms):
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return dict(bytes=nbytes, ms=ms, achieved_gbs=gbs, peak_gbs=HBM_PEAK_GBS, frac=gbs / HBM_PEAK_GBS)
+
+
 def cpu_baseline_sample(w, iters=1):
     """The oracle (numpy/scipy float64) timed on this host for `iters` iterations of workload w."""
     import numpy as np  # noqa: F401
@@ -151,8 +195,11 @@ def run_reference(args, rank, world):
 
 
 def run_ours(args, rank, world, local_rank):
+    import ctypes
+
     import torch
     import torch.distributed as dist
+    from paper_0705_2626_gb300 import capi
     from paper_0705_2626_gb300.solver import Solver
 
     w = args.workload
@@ -162,87 +209,97 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     seed = 2 + rank
-    s = Solver(dims, levels=levels, device=local_rank, precision=args.precision)
-    stream = s.stream
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    # ---- main timed region: K iterations with every column active, inputs resident in HBM
-    s.begin(m, tol=0.0, seed=seed)
-    s.iterate(args.warmup)
-    barrier()
-    torch.cuda.synchronize(dev)
+    def max_over_ranks(x):
+        t = torch.tensor([x], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_form(precision, sampler=None):
+        """K iterations with every column active (tol = 0), inputs resident in HBM; then the same
+        K iterations again with the library's per-phase events for the kernel rooflines."""
+        s = Solver(dims, levels=levels, device=local_rank, precision=precision)
+        s.begin(m, tol=0.0, seed=seed)
+        s.iterate(args.warmup)
+        barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.iterate(args.steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        torch.cuda.synchronize(dev)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = int(s.info.kernel_launches)
+        t_ms = max_over_ranks(e0.elapsed_time(e1))
+        s.set_options(phase_timing=True)
+        s.begin(m, tol=0.0, seed=seed)
+        s.iterate(args.warmup)
+        before = list(s.info.phase_ms)
+        s.iterate(args.steps)
+        after = list(s.info.phase_ms)
+        s.set_options(phase_timing=False)
+        phase = {nm: (after[i] - before[i]) / args.steps for i, nm in enumerate(capi.PHASE_NAMES)}
+        return s, t_ms, launches, phase, clocks
+
+    def time_to_tol(s):
+        out = s.solve(m, tol=1e-8, maxit=300, seed=seed)
+        return out, dict(time_to_tol_s=out["solve_ms"] / 1e3, setup_s=out["setup_ms"] / 1e3, iters=out["iters"],
+                         iters_per_s=out["iters"] / (out["solve_ms"] / 1e3), status=out["status_name"],
+                         max_rel_resid=out["max_rel_resid"], fp64_sweeps=out["fp64_sweeps"], tol=1e-8)
+
+    # ---- float64 form: the timed steps of the JSON line
     sampler = ClockSampler(local_rank)
-    sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.iterate(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize(dev)
-    barrier()
-    clocks = sampler.stop()
-    launches = s.info.kernel_launches
-    t_ms = e0.elapsed_time(e1)
-    tt = torch.tensor([t_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_ms = float(tt.item())
-    value = world * args.steps / (t_ms / 1e3)
-
-    # ---- per-phase device times (events inside the library, same stream) for the roofline
-    s.set_options(phase_timing=True)
-    s.begin(m, tol=0.0, seed=seed)
-    s.iterate(args.warmup)
-    before = list(s.info.phase_ms)
-    s.iterate(args.steps)
-    after = list(s.info.phase_ms)
-    phase = {nm: (after[i] - before[i]) / args.steps for i, nm in enumerate(
-        ["residual", "precond", "cholqr_w", "spmv", "cholqr_p", "gram", "rayleigh_ritz", "update"])}
-    s.set_options(phase_timing=False)
-    gram_ms = phase["gram"]
-    gflop = gram_flops_per_launch(n, m)
-    achieved = gflop / (gram_ms * 1e-3) / 1e12
+    s64, t64, launches, ph64, clocks = timed_form("fp64", sampler)
+    value = world * args.steps / (t64 / 1e3)
+    gram_ms = ph64["gram"]
+    achieved = gram_flops_per_launch(n, m) / (gram_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get((w, kernel_source_hash()))
+    out64, ttt64 = time_to_tol(s64)
 
-    # ---- time to tolerance (tol 1e-8), device time of the iteration loop
-    out = s.solve(m, tol=1e-8, maxit=200, seed=seed)
-    ttt = dict(time_to_tol_s=(out["solve_ms"]) / 1e3, setup_s=out["setup_ms"] / 1e3, iters=out["iters"],
-               status=out["status_name"], max_rel_resid=out["max_rel_resid"], tol=1e-8,
-               fp64_sweeps=out["fp64_sweeps"], lam=out["lam"])
-    other = "mixed" if args.precision == "fp64" else "fp64"
-    so = Solver(dims, levels=levels, device=local_rank, precision=other)
-    oo = so.solve(m, tol=1e-8, maxit=200, seed=seed)
-    so.close()
-    lam_diff = max(abs(a - b) / abs(b) for a, b in zip(oo["lam"], out["lam"]))
-    ttt_other = dict(precision=other, time_to_tol_s=oo["solve_ms"] / 1e3, iters=oo["iters"], status=oo["status_name"],
-                     max_rel_resid=oo["max_rel_resid"], fp64_sweeps=oo["fp64_sweeps"],
-                     max_rel_lambda_diff_vs_timed_form=lam_diff)
-
-    # ---- end to end through the public API with host buffers: X0 from pinned host memory in,
-    # eigenvalues and eigenvectors back to pinned host memory, K iterations (tol 0)
+    # ---- end to end through the public API with host buffers (float64 form): X0 from pinned
+    # host memory in, eigenvalues and eigenvectors back to pinned host memory, K iterations
     X0 = torch.empty((m, n), dtype=torch.float64).pin_memory()
     X0.uniform_(-1.0, 1.0, generator=torch.Generator().manual_seed(seed))
     Xout = torch.empty((m, n), dtype=torch.float64).pin_memory()
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    s.set_initial(X0)
-    s.solve(m, tol=0.0, maxit=args.steps, seed=seed)
-    import ctypes
-    from paper_0705_2626_gb300 import capi
+    s64.set_initial(X0)
+    s64.solve(m, tol=0.0, maxit=args.steps, seed=seed)
     lam = (ctypes.c_double * m)()
-    capi.lobpcg_get_eigenpairs(s.h, lam, ctypes.c_void_p(Xout.data_ptr()), n, 1, None)
-    t_e2e = time.perf_counter() - t0
-    te = torch.tensor([t_e2e], device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = dict(value=world * args.steps / float(te.item()), unit="iters/s",
+    capi.lobpcg_get_eigenpairs(s64.h, lam, ctypes.c_void_p(Xout.data_ptr()), n, 1, None)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = dict(value=world * args.steps / t_e2e, unit="iters/s",
                h2d_bytes_per_step=n * m * 8 / args.steps, d2h_bytes_per_step=(n * m * 8 + m * 8) / args.steps,
-               note="set_initial(host X0) + solve(tol=0, maxit=K) + get_eigenpairs(host), wall clock")
-    s.close()
+               note="set_initial(pinned host X0) + solve(tol=0, maxit=K) + get_eigenpairs(to pinned host), wall clock")
+    s64.close()
+
+    # ---- mixed form (float32 / bfloat16 blocks, double-float X, float64 sweep)
+    smx, tmx, launches_mx, phmx, _ = timed_form("mixed")
+    outmx, tttmx = time_to_tol(smx)
+    smx.close()
+    lam_diff = max(abs(a - b) / abs(b) for a, b in zip(outmx["lam"], out64["lam"]))
+
+    # ---- per-kernel HBM rooflines from the phase events (all m columns active, b = m)
+    q = 3 * m
+    kern64 = dict(spmv_step12=hbm_frac(2 * 8 * n * m, ph64["spmv"]),
+                  vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 8, 8), ph64["precond"]),
+                  gram_steps17_23=hbm_frac(2 * q * 8 * n, ph64["gram"]),
+                  note="float64 stencil and V-cycle are bound by GB300's float64 pipe (1/64 of float32), "
+                       "not by HBM")
+    kernmx = dict(spmv_step12=hbm_frac(2 * 4 * n * m, phmx["spmv"]),
+                  vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 4, 2), phmx["precond"]),
+                  gram_steps17_23=hbm_frac((2 * q + 2 * m) * 4 * n, phmx["gram"]),
+                  update_steps25_33=hbm_frac((2 * m + 2 * m + 3 * m) * 4 * n, phmx["update"]))
 
     if rank != 0:
         return
@@ -254,17 +311,22 @@ def run_ours(args, rank, world, local_rank):
                           "(numpy elementwise single-threaded, BLAS multi-threaded)")
     line = dict(
         metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=t_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f64" if args.precision == "fp64" else "f64+f32+bf16",
-        data="synthetic",
+        ms_per_step=t64 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f64", data="synthetic",
         config=dict(workload=workload_desc(w), grid=list(dims), m=m, levels=levels, tol_timed=0.0,
                     l2="no flush: the 6 stored blocks are 1.6 GB, far above the 129 MB L2",
                     parallelism="replicas" if world > 1 else "single-gpu"),
-        precision=args.precision, time_to_tol=ttt, time_to_tol_other_form=ttt_other, phase_ms_per_iter=phase,
-        roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles)", bound="alu",
+        time_to_tol=dict(fp64=ttt64, mixed=tttmx, mixed_speedup=ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"],
+                         max_rel_lambda_diff_mixed_vs_fp64=lam_diff),
+        mixed=dict(value=world * args.steps / (tmx / 1e3), unit="iters/s", ms_per_step=tmx / args.steps,
+                   dtype="f64+f32+bf16", gpu_launches=launches_mx, phase_ms_per_iter=phmx, kernels_hbm=kernmx),
+        phase_ms_per_iter=ph64, kernels_hbm=kern64,
+        roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles, float64)", bound="alu",
                       achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=achieved / FP64_PEAK_TFLOPS,
-                      traffic=traffic, peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
-        cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
+                      traffic=traffic,
+                      peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
+        hbm_peak_source=HBM_PEAK_SOURCE,
+        cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
     print(json.dumps(line), flush=True)
 
 
@@ -276,8 +338,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="form of the timed steps; the other form's time to tolerance is reported beside it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -28,7 +28,9 @@ namespace {
 
 constexpr int kTX = 32, kTY = 4;
 
-__host__ __device__ inline int zchunk_for(int nz) { return nz >= 64 ? 16 : (nz >= 16 ? 8 : nz); }
+// Planes per thread along k: long runs on large grids (register reuse of the k-1 / k / k+1
+// values), short runs on the small coarse grids, which live in L2 and need the parallelism.
+__host__ __device__ inline int zchunk_for(int nz) { return nz >= 128 ? 16 : (nz >= 32 ? 4 : (nz >= 8 ? 2 : nz)); }
 
 template <typename T, bool HAS_Z>
 __global__ void __launch_bounds__(kTX* kTY)
