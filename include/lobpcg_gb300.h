@@ -55,6 +55,7 @@ extern "C" {
                                       float32 with compensated sums; float64 final check */
 
 #define LOBPCG_LAPLACE7        0   /* constant-coefficient 7-point stencil  */
+#define LOBPCG_VARCOEF7        1   /* -div(kappa grad u), kappa per face     */
 
 #define LOBPCG_PRECOND_NONE    0   /* T = I                                 */
 #define LOBPCG_PRECOND_GMG     1   /* geometric-multigrid V-cycle           */
@@ -117,11 +118,18 @@ typedef struct lobpcg_info {
 int lobpcg_create(lobpcg_t** h, int device, void* stream,
                   const lobpcg_allocator* alloc, int precision);
 
-/* Set the operator A (Section 4, model problem): (A u)_p = scale * (6 u_p -
- * sum of the six neighbours of p), neighbours outside the grid are zero.
- * kind = LOBPCG_LAPLACE7; nx, ny, nz >= 1; scale > 0 (h^-2 = (n+1)^2 for the
- * unit cube; 1.0 gives the unscaled spectrum of Section 4.1).  `kappa_faces`
- * is reserved and must be NULL.  Resets the preconditioner.  Errors: ERR_ARG. */
+/* Set the operator A.  kind = LOBPCG_LAPLACE7 (Section 4, model problem):
+ * (A u)_p = scale * (6 u_p - sum of the six neighbours of p), neighbours
+ * outside the grid are zero; scale > 0 (h^-2 = (n+1)^2 for the unit cube; 1.0
+ * gives the unscaled spectrum of Section 4.1); kappa_faces must be NULL.
+ * kind = LOBPCG_VARCOEF7 (the differentiated operator -div(kappa grad u), unit
+ * spacing, Dirichlet): (A u)_p = scale * sum over the six faces f of p of
+ * kappa_f (u_p - u_q), u_q = 0 outside; kappa_faces points to the face
+ * coefficients (host or device, float64, copied): (nx+1)*ny*nz x-faces, face
+ * (f, j, k) between cells (f-1, j, k) and (f, j, k), then nx*(ny+1)*nz y-faces,
+ * then nx*ny*(nz+1) z-faces, x fastest in each part; all > 0.  VARCOEF7 needs a
+ * LOBPCG_FP64 handle.  nx, ny, nz >= 1.  Resets the preconditioner.
+ * Errors: ERR_ARG, ERR_OOM, ERR_CUDA. */
 int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz,
                         double scale, const double* kappa_faces);
 
@@ -181,6 +189,16 @@ const char* lobpcg_last_error(const lobpcg_t* h);
 
 /* Release the handle and all of its workspace.  NULL is accepted. */
 int lobpcg_destroy(lobpcg_t* h);
+
+/* Eigenvalue gradient of the variable-coefficient operator (LOBPCG_VARCOEF7)
+ * for the finished solve: grad_faces[f] = sum_j w[j] d lambda_j / d kappa_f =
+ * scale * sum_j w[j] (x_j,q - x_j,p)^2 over the m computed unit eigenvectors
+ * (x_j,q = 0 outside the box), the first-order perturbation of a simple
+ * eigenvalue; with equal weights over a cluster of equal eigenvalues the sum is
+ * independent of the basis chosen inside the cluster.  w: host array of m
+ * weights; grad_faces: device array in the kappa_faces layout.  Errors: ERR_ARG,
+ * ERR_STATE (no finished solve, or another operator kind), ERR_CUDA. */
+int lobpcg_eig_grad_kappa(lobpcg_t* h, const double* w, double* grad_faces);
 
 /* ---- kernel-level entry points -------------------------------------------
  * Each applies one step of the iteration to caller-owned device buffers, on

@@ -19,7 +19,7 @@ ERR_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_NONFINITE, ERR_STATE, ERR_TIMEOUT
 STATUS_NAMES = {0: "ok", 1: "not_converged", -1: "err_arg", -2: "err_oom", -3: "err_cuda",
                 -4: "breakdown", -5: "nonfinite", -6: "err_state", -7: "err_timeout"}
 FP64, MIXED = 0, 1
-LAPLACE7 = 0
+LAPLACE7, VARCOEF7 = 0, 1
 PRECOND_NONE, PRECOND_GMG = 0, 1
 TOL_RELATIVE, TOL_ABSOLUTE = 0, 1
 GRAM_EXPLICIT, GRAM_PAPER = 0, 1
@@ -53,6 +53,7 @@ _SIGNATURES = {
     "lobpcg_iterate": (c_int, [c_void_p, c_int, ctypes.POINTER(Info)]),
     "lobpcg_finish": (c_int, [c_void_p, ctypes.POINTER(Info)]),
     "lobpcg_get_eigenpairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_void_p]),
+    "lobpcg_eig_grad_kappa": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lobpcg_last_error": (ctypes.c_char_p, [c_void_p]),
     "lobpcg_destroy": (c_int, [c_void_p]),
     "lobpcg_op_random_block": (c_int, [c_void_p, c_uint64, c_int, c_void_p, c_int64]),
@@ -168,6 +169,10 @@ def lobpcg_op_residual(h, ncols, cols, X, AX, ld, lam, W, ldw, norms):
 
 def lobpcg_op_gram(h, S0, S1, S2, AS0, AS1, AS2, ld, w0, w1, w2, gramA, gramB):
     return _call("lobpcg_op_gram", h, S0, S1, S2, AS0, AS1, AS2, ld, w0, w1, w2, gramA, gramB)
+
+
+def lobpcg_eig_grad_kappa(h, w, grad_faces):
+    return _call("lobpcg_eig_grad_kappa", h, w, grad_faces)
 
 
 def lobpcg_op_gram_f32(h, S0, w0, S1, w1, V, b, ld, C, G):

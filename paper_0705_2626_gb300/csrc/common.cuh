@@ -192,6 +192,26 @@ void launch_apply32(int64_t n, int b, float* V, int64_t ld, const double* Rinv,
 void launch_update_mx2(int64_t n, int m, float* Xh, float* Xl, const float* W, int b, const float* P,
                        int bp, int64_t ld, const double* C, int q, float* Pout, const unsigned* status,
                        unsigned skip, unsigned* err, cudaStream_t st);
+// ---------------------------------------------------------------- variable coefficients
+// (k_varcoef.cu).  Face coefficients in the layout x-, y-, z-faces (x fastest), float64.
+int64_t vc_num_faces(const Grid3& g);
+// mode 0: y = A x;  1: y = (1-w) x + w (z/scale + N x)/D (Jacobi, e = x, r = z);
+// 2: y = z - A x;  3: y = w z / (scale D)  -- A = scale (D - N), D = sum of the 6 faces.
+void launch_vc_sweep(const Grid3& g, int mode, int ncols, const double* kap, double scale, double w,
+                     const double* x, int64_t ldx, const double* z, int64_t ldz, double* y,
+                     int64_t ldy, cudaStream_t st);
+// Coarse-level faces (harmonic along the normal, 1/4-1/2-1/4 across, / 4).
+void launch_vc_coarsen(const Grid3& gf, const Grid3& gc, const double* kf, double* kc, cudaStream_t st);
+// Ainv = A^-1 of the operator on the (small) grid g via a dense Cholesky factor; A and work are
+// n x n scratch; *fail set if A is not positive definite.
+void launch_vc_coarse_inverse(const Grid3& g, const double* kap, double scale, double* A, double* work,
+                              double* Ainv, int* fail, cudaStream_t st);
+// e = Ainv r for ncols columns (Ainv n x n column-major).
+void launch_dense_apply(int n, int ncols, const double* Ainv, const double* r, int64_t ldr, double* e,
+                        int64_t lde, cudaStream_t st);
+// grad[f] = scale sum_i w[i] (x_i,q - x_i,p)^2 (w host array of m weights).
+void launch_vc_grad(const Grid3& g, int m, const double* w, double scale, const double* X, int64_t ldx,
+                    double* grad, cudaStream_t st);
 // ---------------------------------------------------------------- small dense
 // Rinv = R^-1, R = chol(G) on the unit-diagonal scaling of G (b x b).  On failure sets
 // fail_bit in *status and leaves Rinv unspecified.  Skipped if *status & skip_mask.

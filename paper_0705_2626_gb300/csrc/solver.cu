@@ -68,6 +68,10 @@ struct lobpcg_handle {
     std::vector<Grid3> lv;
     std::vector<double> lscale;
     Buf coarse_tab;
+    // variable-coefficient operator: face coefficients per level, dense inverse of the coarsest
+    bool varcoef = false;
+    std::vector<Buf> lkap;
+    Buf vc_inv;
     // options
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
 
@@ -160,6 +164,13 @@ void free_workspace(lobpcg_t* h) {
     h->status = nullptr;
 }
 
+void free_varcoef(lobpcg_t* h) {
+    for (auto& b : h->lkap) dfree(h, b);
+    h->lkap.clear();
+    dfree(h, h->vc_inv);
+    h->varcoef = false;
+}
+
 // Workspace for blocks of up to wm columns (6m vectors of the algorithm + V-cycle buffers).
 void ensure_workspace(lobpcg_t* h, int wm) {
     if (h->wm >= wm && h->X.p) return;
@@ -221,9 +232,15 @@ ColList identity_cols(int b) {
 
 // ------------------------------------------------------------------ operator and T
 void spmv(lobpcg_t* h, int ncols, DType t, const void* x, int64_t ldx, void* y, int64_t ldy) {
+    if (h->varcoef) {
+        launch_vc_sweep(h->g, 0, ncols, f64(h->lkap[0]), h->scale, 0.0, static_cast<const double*>(x), ldx,
+                        nullptr, 0, static_cast<double*>(y), ldy, h->stream);
+        return;
+    }
     launch_stencil_axpby(h->g, ncols, t, 6.0 * h->scale, -h->scale, x, ldx, 0.0, nullptr, 0, y, ldy,
                          h->stream);
 }
+
 
 void copy_cols(lobpcg_t* h, int ncols, int64_t n, DType t, const void* src, int64_t lds, void* dst,
                int64_t ldd) {
@@ -234,6 +251,44 @@ void copy_cols(lobpcg_t* h, int ncols, int64_t n, DType t, const void* src, int6
 
 void* col(const Buf& b, DType t, int64_t ld, int j) {
     return static_cast<char*>(b.p) + (size_t)j * ld * dtype_size(t);
+}
+
+// V-cycle of the variable-coefficient operator on level l (float64): the steps of vcycle()
+// below with the face-coefficient sweeps; the first two pre-smoothing sweeps are not fused.
+void vcycle_vc(lobpcg_t* h, int l, int b, const double* r, int64_t ldr, double* e, int64_t lde, double* tmp,
+               int64_t ldt) {
+    const Grid3& g = h->lv[l];
+    const int L = (int)h->lv.size();
+    if (l == L - 1) {
+        launch_dense_apply((int)g.n(), b, f64(h->vc_inv), r, ldr, e, lde, h->stream);
+        return;
+    }
+    const double s = h->scale, w = h->omega;
+    const double* kap = f64(h->lkap[l]);
+    double* cur = e;
+    int64_t ldc = lde;
+    double* oth = tmp;
+    int64_t ldo = ldt;
+    launch_vc_sweep(g, 3, b, kap, s, w, nullptr, 0, r, ldr, cur, ldc, h->stream);      // from e = 0
+    for (int k = 1; k < h->nu_pre; ++k) {
+        launch_vc_sweep(g, 1, b, kap, s, w, cur, ldc, r, ldr, oth, ldo, h->stream);
+        std::swap(cur, oth);
+        std::swap(ldc, ldo);
+    }
+    launch_vc_sweep(g, 2, b, kap, s, w, cur, ldc, r, ldr, oth, ldo, h->stream);        // r - A e
+    const Grid3& gc = h->lv[l + 1];
+    double* rc = f64(h->lr[l + 1]);
+    double* ec = f64(h->le[l + 1]);
+    const int64_t ldl = h->lld[l + 1];
+    launch_restrict(g, gc, b, DT_F64, oth, ldo, DT_F64, rc, ldl, h->stream);
+    vcycle_vc(h, l + 1, b, rc, ldl, ec, ldl, f64(h->lt[l + 1]), ldl);
+    launch_prolong_add(g, gc, b, DT_F64, ec, ldl, DT_F64, cur, ldc, h->stream);
+    for (int k = 0; k < h->nu_post; ++k) {
+        launch_vc_sweep(g, 1, b, kap, s, w, cur, ldc, r, ldr, oth, ldo, h->stream);
+        std::swap(cur, oth);
+        std::swap(ldc, ldo);
+    }
+    if (cur != e) copy_cols(h, b, g.n(), DT_F64, cur, ldc, e, lde);
 }
 
 // V-cycle on level l: e = T_l r for b columns of type t.  tmp is a scratch block of the same shape.
@@ -286,6 +341,11 @@ void precond(lobpcg_t* h, int b, DType t, const void* r, int64_t ldr, void* e, i
              void* tmp, int64_t ldt) {
     if (h->pc_kind == LOBPCG_PRECOND_NONE) {
         copy_cols(h, b, h->g.n(), t, r, ldr, e, lde);
+        return;
+    }
+    if (h->varcoef) {
+        vcycle_vc(h, 0, b, static_cast<const double*>(r), ldr, static_cast<double*>(e), lde,
+                  static_cast<double*>(tmp), ldt);
         return;
     }
     vcycle(h, 0, b, t, r, ldr, e, lde, tmp, ldt);
@@ -801,17 +861,31 @@ int lobpcg_create(lobpcg_t** out, int device, void* stream, const lobpcg_allocat
 int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz, double scale,
                         const double* kappa_faces) {
     return guarded(h, [&] {
-        LG_REQUIRE(kind == LOBPCG_LAPLACE7, LOBPCG_ERR_ARG, "unknown operator kind");
-        LG_REQUIRE(kappa_faces == nullptr, LOBPCG_ERR_ARG, "kappa_faces must be NULL for LAPLACE7");
+        LG_REQUIRE(kind == LOBPCG_LAPLACE7 || kind == LOBPCG_VARCOEF7, LOBPCG_ERR_ARG, "unknown operator kind");
+        LG_REQUIRE(kind == LOBPCG_VARCOEF7 || kappa_faces == nullptr, LOBPCG_ERR_ARG,
+                   "kappa_faces must be NULL for LAPLACE7");
+        LG_REQUIRE(kind == LOBPCG_LAPLACE7 || kappa_faces != nullptr, LOBPCG_ERR_ARG,
+                   "VARCOEF7 needs kappa_faces");
+        LG_REQUIRE(kind == LOBPCG_LAPLACE7 || h->precision == LOBPCG_FP64, LOBPCG_ERR_ARG,
+                   "VARCOEF7 needs a LOBPCG_FP64 handle");
         LG_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1, LOBPCG_ERR_ARG, "grid dimensions must be >= 1");
         LG_REQUIRE((int64_t)nx * ny * nz <= (int64_t)1 << 31, LOBPCG_ERR_ARG, "grid too large");
         LG_REQUIRE(scale > 0.0 && std::isfinite(scale), LOBPCG_ERR_ARG, "scale must be > 0");
         free_workspace(h);
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
+        free_varcoef(h);
         h->X0_m = 0;
         h->g = Grid3{nx, ny, nz};
         h->scale = scale;
+        if (kind == LOBPCG_VARCOEF7) {
+            const size_t bytes = (size_t)vc_num_faces(h->g) * sizeof(double);
+            h->lkap.assign(1, Buf{});
+            ensure(h, h->lkap[0], bytes);
+            LG_CUDA(cudaMemcpyAsync(h->lkap[0].p, kappa_faces, bytes, cudaMemcpyDefault, h->stream));
+            LG_CUDA(cudaStreamSynchronize(h->stream));
+            h->varcoef = true;
+        }
         h->has_op = true;
         h->pc_kind = LOBPCG_PRECOND_NONE;
         h->lv.assign(1, h->g);
@@ -829,6 +903,9 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre, int
                    "unknown preconditioner kind");
         free_workspace(h);
         dfree(h, h->coarse_tab);
+        for (size_t l = 1; l < h->lkap.size(); ++l) dfree(h, h->lkap[l]);
+        if (h->varcoef) h->lkap.resize(1);
+        dfree(h, h->vc_inv);
         h->lv.assign(1, h->g);
         h->lscale.assign(1, h->scale);
         h->pc_kind = LOBPCG_PRECOND_NONE;
@@ -847,16 +924,38 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre, int
             lv.push_back(c);
             ls.push_back(ls.back() / 4.0);
         }
-        LG_REQUIRE(lv.back().n() <= 4096, LOBPCG_ERR_ARG,
-                   "coarsest level has more than 4096 points; use more levels");
+        LG_REQUIRE(lv.back().n() <= (h->varcoef ? 512 : 4096), LOBPCG_ERR_ARG,
+                   h->varcoef ? "coarsest level has more than 512 points; use more levels"
+                              : "coarsest level has more than 4096 points; use more levels");
         h->lv = lv;
         h->lscale = ls;
         h->levels = levels;
         h->nu_pre = nu_pre;
         h->nu_post = nu_post;
         h->omega = omega;
-        ensure(h, h->coarse_tab, coarse_tables_size(lv.back()) * sizeof(double));
-        launch_coarse_setup(lv.back(), ls.back(), f64(h->coarse_tab), h->stream);
+        if (h->varcoef) {
+            // coarse face coefficients level by level, then the dense inverse of the coarsest
+            h->lkap.resize(1);
+            for (int l = 1; l < levels; ++l) {
+                h->lkap.push_back(Buf{});
+                ensure(h, h->lkap[l], (size_t)vc_num_faces(lv[l]) * sizeof(double));
+                launch_vc_coarsen(lv[l - 1], lv[l], f64(h->lkap[l - 1]), f64(h->lkap[l]), h->stream);
+            }
+            const int64_t nc = lv.back().n();
+            ensure(h, h->vc_inv, (size_t)(3 * nc * nc + 2) * sizeof(double));
+            double* A = f64(h->vc_inv) + nc * nc;
+            int* fail = reinterpret_cast<int*>(f64(h->vc_inv) + 3 * nc * nc);
+            LG_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), h->stream));
+            launch_vc_coarse_inverse(lv.back(), f64(h->lkap.back()), h->scale, A, A + nc * nc, f64(h->vc_inv), fail,
+                                     h->stream);
+            int fail_h = 0;
+            LG_CUDA(cudaMemcpyAsync(&fail_h, fail, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            LG_CUDA(cudaStreamSynchronize(h->stream));
+            LG_REQUIRE(!fail_h, LOBPCG_ERR_ARG, "coarsest operator is not positive definite (kappa must be > 0)");
+        } else {
+            ensure(h, h->coarse_tab, coarse_tables_size(lv.back()) * sizeof(double));
+            launch_coarse_setup(lv.back(), ls.back(), f64(h->coarse_tab), h->stream);
+        }
         h->pc_kind = LOBPCG_PRECOND_GMG;
         h->state = 0;
         return LOBPCG_OK;
@@ -967,6 +1066,18 @@ int lobpcg_get_eigenpairs(lobpcg_t* h, double* lambda, double* X, int64_t ldx, i
     });
 }
 
+int lobpcg_eig_grad_kappa(lobpcg_t* h, const double* w, double* grad_faces) {
+    return guarded(h, [&] {
+        LG_REQUIRE(h->state == 2, LOBPCG_ERR_STATE, "no finished solve on this handle");
+        LG_REQUIRE(h->varcoef, LOBPCG_ERR_STATE, "the operator is not LOBPCG_VARCOEF7");
+        LG_REQUIRE(w && grad_faces, LOBPCG_ERR_ARG, "w and grad_faces must not be NULL");
+        for (int j = 0; j < h->m; ++j) LG_REQUIRE(std::isfinite(w[j]), LOBPCG_ERR_ARG, "non-finite weight");
+        launch_vc_grad(h->g, h->m, w, h->scale, f64(h->X), h->ld, grad_faces, h->stream);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
 const char* lobpcg_last_error(const lobpcg_t* h) {
     if (!h) return g_handle_free_error.c_str();
     return h->err.c_str();
@@ -979,6 +1090,7 @@ int lobpcg_destroy(lobpcg_t* h) {
         free_workspace(h);
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
+        free_varcoef(h);
         cudaStreamSynchronize(h->stream);
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);

@@ -58,13 +58,17 @@ class Solver:
 
     def __init__(self, dims, scale=None, precond="gmg", levels=None, nu=2, omega=2.0 / 3.0,
                  device=0, stream=None, tol_mode="relative", gram="explicit", phase_timing=False,
-                 torch_allocator=True, precision="fp64"):
+                 torch_allocator=True, precision="fp64", kappa=None):
+        """kappa: face coefficients of the variable-coefficient operator -div(kappa grad u) (unit
+        spacing; layout of paper_0705_2626_gb300.fields), a float64 numpy array or torch tensor;
+        None selects the constant-coefficient Laplacian."""
         if precision not in ("fp64", "mixed"):
             raise ValueError(f"precision must be 'fp64' or 'mixed', not {precision!r}")
         self.precision = precision
         self.dims = tuple(int(d) for d in dims)
         self.n = self.dims[0] * self.dims[1] * self.dims[2]
-        self.scale = default_scale(self.dims) if scale is None else float(scale)
+        self.varcoef = kappa is not None
+        self.scale = (1.0 if self.varcoef else default_scale(self.dims)) if scale is None else float(scale)
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._alloc = _TorchAllocator(device) if torch_allocator else None
@@ -73,13 +77,24 @@ class Solver:
                                   ctypes.byref(self._alloc.struct) if self._alloc else None,
                                   capi.MIXED if precision == "mixed" else capi.FP64))
         self.h = h
-        _check(capi.lobpcg_set_operator(h, capi.LAPLACE7, *self.dims, self.scale, None), h)
+        if self.varcoef:
+            kt = torch.as_tensor(kappa, dtype=torch.float64)
+            kt = kt.detach().to(self.device).contiguous()
+            torch.cuda.current_stream(self.device).synchronize()
+            _check(capi.lobpcg_set_operator(h, capi.VARCOEF7, *self.dims, self.scale,
+                                            ctypes.c_void_p(kt.data_ptr())), h)
+        else:
+            _check(capi.lobpcg_set_operator(h, capi.LAPLACE7, *self.dims, self.scale, None), h)
         if precond == "gmg":
             if levels is None:
                 levels = 1
-                d = min(self.dims)
-                while d // 2 >= 3 and levels < 24:
-                    d //= 2
+                d = list(self.dims)
+                while min(d) // 2 >= 3 and levels < 24:
+                    d = [x // 2 for x in d]
+                    levels += 1
+                # the variable-coefficient coarsest level is solved with a dense inverse
+                while self.varcoef and d[0] * d[1] * d[2] > 512 and min(d) // 2 >= 1:
+                    d = [x // 2 for x in d]
                     levels += 1
             _check(capi.lobpcg_set_preconditioner(h, capi.PRECOND_GMG, levels, nu, nu, omega), h)
         elif precond is None or precond == "none":
@@ -119,11 +134,11 @@ class Solver:
         _check(capi.lobpcg_set_initial(self.h, ctypes.c_void_p(X0.data_ptr()), X0.shape[0], X0.shape[1],
                                        on_host), self.h)
 
-    def solve(self, m, tol=1e-8, maxit=200, seed=2):
+    def solve(self, m, tol=1e-8, maxit=200, seed=2, with_vectors=True):
         rc = capi.lobpcg_solve(self.h, m, tol, maxit, seed, ctypes.byref(self.info))
         self.m = m
         _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
-        return self.result()
+        return self.result(with_vectors)
 
     def begin(self, m, tol=1e-8, seed=2):
         _check(capi.lobpcg_begin(self.h, m, tol, seed), self.h)
@@ -143,6 +158,18 @@ class Solver:
         rc = capi.lobpcg_finish(self.h, ctypes.byref(self.info))
         _check(rc, self.h, allow=(capi.OK, capi.NOT_CONVERGED))
         return rc
+
+    def eig_grad(self, w):
+        """Gradient of sum_j w[j] lambda_j with respect to the face coefficients (variable-
+        coefficient operator, after a finished solve), as a float64 tensor on the device."""
+        w = [float(x) for x in w]
+        assert len(w) == self.m
+        wa = (ctypes.c_double * self.m)(*w)
+        from .fields import num_faces
+        g = torch.empty(num_faces(self.dims), dtype=torch.float64, device=self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+        _check(capi.lobpcg_eig_grad_kappa(self.h, wa, ctypes.c_void_p(g.data_ptr())), self.h)
+        return g
 
     def result(self, with_vectors=True):
         m = self.m
