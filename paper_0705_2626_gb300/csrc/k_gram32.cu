@@ -20,6 +20,7 @@
 //    as an unevaluated pair (hi, lo) updated by Knuth's two-sum -- about 2^-44 relative.
 //    These are written with the _rn intrinsics so that no multiply is contracted into an add.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -108,7 +109,7 @@ template <>
 struct TileShape<true> { static constexpr int TI = 4, TJ = 4; };
 
 template <bool DF>
-__global__ void __launch_bounds__(kG32Threads, 1)
+__global__ void __launch_bounds__(kG32Threads, DF ? 1 : 2)
     k_gram32(const __grid_constant__ G32Args a, int64_t n, double* __restrict__ part, unsigned* status) {
     constexpr int TI = TileShape<DF>::TI, TJ = TileShape<DF>::TJ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -145,11 +146,19 @@ __global__ void __launch_bounds__(kG32Threads, 1)
     if (tid == 0)
         for (int st = 0; st < min(nst, a.nstage); ++st) issue(st);
 
+    // float32 tiles: acc = the current run's sums, tot = Kahan total, cmpb = its compensation
+    // kept as bfloat16 pairs (the compensation is ~eps32 |tot|; rounding it to 8 bits changes the
+    // total by ~2^-9 eps32 |tot| per flush, and halves its registers so that two blocks fit per
+    // SM).  Double-float tiles: tot / cmp = hi / lo of the running sums.
     float acc[TI][TJ], tot[TI][TJ], cmp[TI][TJ];
+    __nv_bfloat162 cmpb[TI][TJ / 2];
 #pragma unroll
-    for (int u = 0; u < TI; ++u)
+    for (int u = 0; u < TI; ++u) {
 #pragma unroll
         for (int v = 0; v < TJ; ++v) acc[u][v] = tot[u][v] = cmp[u][v] = 0.f;
+#pragma unroll
+        for (int v = 0; v < TJ / 2; ++v) cmpb[u][v] = __floats2bfloat162_rn(0.f, 0.f);
+    }
 
     const int steps = a.K / (4 * a.ks);                       // float4 steps per lane and stage
     const int flush_every = max(1, (32 * a.ks) / a.K);        // >= 32 rows per float32 run
@@ -208,12 +217,17 @@ __global__ void __launch_bounds__(kG32Threads, 1)
 #pragma unroll
                     for (int u = 0; u < TI; ++u)
 #pragma unroll
-                        for (int v = 0; v < TJ; ++v) {
-                            const float y = __fsub_rn(acc[u][v], cmp[u][v]);
-                            const float t = __fadd_rn(tot[u][v], y);
-                            cmp[u][v] = __fsub_rn(__fsub_rn(t, tot[u][v]), y);
-                            tot[u][v] = t;
-                            acc[u][v] = 0.f;
+                        for (int v = 0; v < TJ; v += 2) {
+                            float c2[2] = {__low2float(cmpb[u][v / 2]), __high2float(cmpb[u][v / 2])};
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float y = __fsub_rn(acc[u][v + e], c2[e]);
+                                const float t = __fadd_rn(tot[u][v + e], y);
+                                c2[e] = __fsub_rn(__fsub_rn(t, tot[u][v + e]), y);
+                                tot[u][v + e] = t;
+                                acc[u][v + e] = 0.f;
+                            }
+                            cmpb[u][v / 2] = __floats2bfloat162_rn(c2[0], c2[1]);
                         }
                 }
             }
@@ -240,7 +254,13 @@ __global__ void __launch_bounds__(kG32Threads, 1)
     for (int u = 0; u < TI; ++u)
 #pragma unroll
         for (int v = 0; v < TJ; ++v) {
-            double r = DF ? (double)tot[u][v] + (double)cmp[u][v] : (double)tot[u][v] - (double)cmp[u][v];
+            double r;
+            if constexpr (DF) {
+                r = (double)tot[u][v] + (double)cmp[u][v];
+            } else {
+                const float c = (v & 1) ? __high2float(cmpb[u][v / 2]) : __low2float(cmpb[u][v / 2]);
+                r = (double)tot[u][v] - (double)c;
+            }
             for (int off = a.ks >> 1; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
             const int i = i0 + u - o.lbase, j = j0 + v - o.rbase;
             if (active && kg == 0 && g32_need(o, i, j)) dst[i + (int64_t)o.ld * j] = r;
@@ -314,7 +334,8 @@ void g32_launch(G32Args& a, int64_t n, int64_t ld, const G32Block* blk, int nblk
     a.tpc = std::min(a.ntiles, kG32Threads / a.ks);
     a.ngroups = (a.ntiles + a.tpc - 1) / a.tpc;
     const int64_t stage_bytes = (int64_t)Q * a.K * sizeof(float);
-    a.nstage = (int)std::max<int64_t>(2, std::min<int64_t>(6, (kG32SmemBudget - kG32Header) / stage_bytes));
+    const int64_t budget = DF ? kG32SmemBudget : kG32SmemBudget / 2;    // two float32 blocks per SM
+    a.nstage = (int)std::max<int64_t>(2, std::min<int64_t>(6, (budget - 2 * kG32Header) / stage_bytes));
     LG_REQUIRE(2 * kG32Header + a.nstage * stage_bytes <= 227 * 1024, LOBPCG_ERR_ARG, "Gram stage too large");
     a.rows_per_chunk = ceil_div(ceil_div(n, nchunks), 128) * 128;
     // encode the column blocks (rows beyond n read as zeros)
