@@ -92,6 +92,16 @@ int64_t coarse_tables_size(const Grid3& g);
 void launch_coarse_setup(const Grid3& g, double scale, double* tables, cudaStream_t st);
 void launch_coarse_solve(const Grid3& g, int ncols, DType t, const double* tables, const void* r,
                          int64_t ldr, void* e, int64_t lde, cudaStream_t st);
+// The V-cycle on the levels g[0..nl-1] (g[0] the finest of them, scales[l] their operator scales,
+// tables = the sine-transform tables of g[nl-1]) in one kernel, one block per column, all level
+// vectors in shared memory: e = T r for ncols columns of type t (input and output only touch
+// global memory).  For levels of at most kFuseMaxPoints points.
+constexpr int kFuseMaxPoints = 4096;
+constexpr int kFuseMaxLevels = 12;
+size_t vcycle_small_smem(const Grid3* g, int nl, DType t);
+void launch_vcycle_small(const Grid3* g, const double* scales, int nl, double omega, int nu_pre, int nu_post,
+                         const double* tables, int ncols, DType t, const void* r, int64_t ldr, void* e,
+                         int64_t lde, cudaStream_t st);
 // Copy (with conversion) of ncols columns of n entries.
 void launch_convert(int64_t n, int ncols, DType ts, const void* src, int64_t lds, DType td,
                     void* dst, int64_t ldd, cudaStream_t st);

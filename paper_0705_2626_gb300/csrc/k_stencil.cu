@@ -318,6 +318,191 @@ __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const T*
     for (int p = threadIdx.x; p < n; p += blockDim.x) st_as(e + (int64_t)col * lde + p, u[p]);
 }
 
+// ---------------------------------------------------------------- small levels, fused
+// The coarse end of the V-cycle (every level with at most kFuseMaxPoints points and the levels
+// below it) in one kernel: one thread block per column keeps all of its level vectors in shared
+// memory (compute type C: float for float32 / bfloat16 storage, double for float64) and runs the
+// same steps as the multi-kernel path -- fused first two pre-sweeps, Jacobi sweeps, residual,
+// full-weighting restriction, exact sine-transform solve on the coarsest level, trilinear
+// prolongation, post-sweeps -- separated by block barriers instead of kernel launches.
+struct SmallLevels {
+    int nl;
+    Grid3 g[kFuseMaxLevels];
+    double s[kFuseMaxLevels];
+    int off[kFuseMaxLevels];    // element offset of level l's three vectors (r, e, t)
+};
+
+template <typename C>
+__device__ void sm_axpby(const Grid3& g, C a, C b, const C* x, C c, const C* z, C* y) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, n = nx * ny * nz, sy = nx, sz = nx * ny;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int i = p % nx, j = (p / nx) % ny, k = p / sz;
+        const C x0 = x[p];
+        const C xm = k > 0 ? x[p - sz] : C(0), xp = k + 1 < nz ? x[p + sz] : C(0);
+        C v;
+        if constexpr (sizeof(C) == 8) {
+            C nb = xm + xp;
+            if (i > 0) nb += x[p - 1];
+            if (i + 1 < nx) nb += x[p + 1];
+            if (j > 0) nb += x[p - sy];
+            if (j + 1 < ny) nb += x[p + sy];
+            v = fma(b, nb, a * x0);
+        } else {
+            C d = (x0 - xm) + (x0 - xp);
+            d += i > 0 ? x0 - x[p - 1] : x0;
+            d += i + 1 < nx ? x0 - x[p + 1] : x0;
+            d += j > 0 ? x0 - x[p - sy] : x0;
+            d += j + 1 < ny ? x0 - x[p + sy] : x0;
+            v = fma(-b, d, (a + C(6) * b) * x0);
+        }
+        if (z) v = fma(c, z[p], v);
+        y[p] = v;
+    }
+    __syncthreads();
+}
+
+template <typename C>
+__device__ void sm_restrict(const Grid3& gf, const Grid3& gc, const C* f, C* rc) {
+    const int nc = gc.n();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        const int I = q % gc.nx, J = (q / gc.nx) % gc.ny, K = q / (gc.nx * gc.ny);
+        const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
+        C sacc = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int kk = fk + dz;
+            if (kk >= gf.nz) continue;
+            const C wz = dz == 0 ? C(1) : C(0.5);
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int jj = fj + dy;
+                if (jj >= gf.ny) continue;
+                const C wzy = wz * (dy == 0 ? C(1) : C(0.5));
+                const int row = gf.nx * (jj + gf.ny * kk);
+                C t = f[row + fi];
+                if (fi - 1 >= 0) t = fma(C(0.5), f[row + fi - 1], t);
+                if (fi + 1 < gf.nx) t = fma(C(0.5), f[row + fi + 1], t);
+                sacc = fma(wzy, t, sacc);
+            }
+        }
+        rc[q] = C(0.125) * sacc;
+    }
+    __syncthreads();
+}
+
+// fine index f0 (0-based) -> coarse taps (index, weight) of the trilinear prolongation
+__device__ __forceinline__ void sm_taps(int f0, int nc, int& i0, int& i1, float& w0, float& w1) {
+    const int f = f0 + 1;
+    if ((f & 1) == 0) {
+        const int I = f >> 1;
+        i0 = I - 1; w0 = I <= nc ? 1.0f : 0.0f;
+        i1 = i0;    w1 = 0.0f;
+    } else {
+        const int I1 = (f - 1) >> 1, I2 = (f + 1) >> 1;
+        i0 = I1 - 1; w0 = I1 >= 1 ? 0.5f : 0.0f;
+        i1 = I2 - 1; w1 = I2 <= nc ? 0.5f : 0.0f;
+    }
+    i0 = max(0, min(i0, nc - 1));
+    i1 = max(0, min(i1, nc - 1));
+}
+
+template <typename C>
+__device__ void sm_prolong_add(const Grid3& gf, const Grid3& gc, const C* ec, C* ef) {
+    const int nf = gf.n();
+    for (int p = threadIdx.x; p < nf; p += blockDim.x) {
+        const int i = p % gf.nx, j = (p / gf.nx) % gf.ny, k = p / (gf.nx * gf.ny);
+        int xi[2], yi[2], zi[2];
+        float xw[2], yw[2], zw[2];
+        sm_taps(i, gc.nx, xi[0], xi[1], xw[0], xw[1]);
+        sm_taps(j, gc.ny, yi[0], yi[1], yw[0], yw[1]);
+        sm_taps(k, gc.nz, zi[0], zi[1], zw[0], zw[1]);
+        C sacc = 0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const C w = C(zw[a]) * C(yw[b]);
+                const int row = gc.nx * (yi[b] + gc.ny * zi[a]);
+#pragma unroll
+                for (int d = 0; d < 2; ++d) sacc = fma(w * C(xw[d]), ec[row + xi[d]], sacc);
+            }
+        ef[p] += sacc;
+    }
+    __syncthreads();
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(512)
+    k_vcycle_small(SmallLevels L, double omega, int nu_pre, int nu_post, const double* __restrict__ tab,
+                   const T* __restrict__ r, int64_t ldr, T* __restrict__ e, int64_t lde) {
+    extern __shared__ __align__(16) double smd[];
+    const Grid3 gc = L.g[L.nl - 1];
+    const int ncs = gc.n();
+    double* u = smd;                     // sine-transform scratch of the coarsest level
+    double* v = smd + ncs;
+    C* sm = reinterpret_cast<C*>(smd + 2 * ncs);
+    const int col = blockIdx.x;
+    const int n0 = L.g[0].n();
+    C* R0 = sm + L.off[0];
+    for (int p = threadIdx.x; p < n0; p += blockDim.x) R0[p] = C(ld_as(r + (int64_t)col * ldr + p));
+    __syncthreads();
+    C* fin[kFuseMaxLevels];    // final e of each level
+    C* oth[kFuseMaxLevels];
+    const C w = C(omega);
+    for (int l = 0; l < L.nl - 1; ++l) {
+        const Grid3 g = L.g[l];
+        const int nl = g.n();
+        const C s = C(L.s[l]), alpha = C(omega / (6.0 * L.s[l]));
+        C* Rl = sm + L.off[l];
+        C* c = Rl + nl;
+        C* o = Rl + 2 * nl;
+        int done;
+        if (nu_pre >= 2) { sm_axpby(g, alpha * (C(2) - w), alpha * w / C(6), Rl, C(0), (const C*)nullptr, c); done = 2; }
+        else { sm_axpby(g, alpha, C(0), Rl, C(0), (const C*)nullptr, c); done = 1; }
+        for (; done < nu_pre; ++done) {
+            sm_axpby(g, C(1) - w, w / C(6), c, alpha, Rl, o);
+            C* t = c; c = o; o = t;
+        }
+        sm_axpby(g, -C(6) * s, s, c, C(1), Rl, o);          // residual r - A e
+        sm_restrict(g, L.g[l + 1], o, sm + L.off[l + 1]);
+        fin[l] = c;
+        oth[l] = o;
+    }
+    {   // coarsest: e = Q diag(1/lambda) Q r
+        const C* Rc = sm + L.off[L.nl - 1];
+        C* Ec = sm + L.off[L.nl - 1] + ncs;
+        const double* Qx = tab;
+        const double* Qy = Qx + gc.nx * gc.nx;
+        const double* Qz = Qy + gc.ny * gc.ny;
+        const double* lam = Qz + gc.nz * gc.nz;
+        for (int p = threadIdx.x; p < ncs; p += blockDim.x) u[p] = (double)Rc[p];
+        __syncthreads();
+        sine_pass(gc, 0, Qx, u, v);
+        sine_pass(gc, 1, Qy, v, u);
+        sine_pass(gc, 2, Qz, u, v);
+        for (int p = threadIdx.x; p < ncs; p += blockDim.x) v[p] /= lam[p];
+        __syncthreads();
+        sine_pass(gc, 0, Qx, v, u);
+        sine_pass(gc, 1, Qy, u, v);
+        sine_pass(gc, 2, Qz, v, u);
+        for (int p = threadIdx.x; p < ncs; p += blockDim.x) Ec[p] = C(u[p]);
+        __syncthreads();
+        fin[L.nl - 1] = Ec;
+    }
+    for (int l = L.nl - 2; l >= 0; --l) {
+        const Grid3 g = L.g[l];
+        const C alpha = C(omega / (6.0 * L.s[l]));
+        C* Rl = sm + L.off[l];
+        C* c = fin[l];
+        C* o = oth[l];
+        sm_prolong_add(g, L.g[l + 1], fin[l + 1], c);
+        for (int k = 0; k < nu_post; ++k) {
+            sm_axpby(g, C(1) - w, w / C(6), c, alpha, Rl, o);
+            C* t = c; c = o; o = t;
+        }
+        fin[l] = c;
+    }
+    for (int p = threadIdx.x; p < n0; p += blockDim.x) st_as(e + (int64_t)col * lde + p, fin[0][p]);
+}
+
 template <typename TS, typename TD>
 __global__ void k_convert(int64_t n, int ncols, const TS* __restrict__ src, int64_t lds,
                           TD* __restrict__ dst, int64_t ldd) {
@@ -459,4 +644,43 @@ void launch_convert(int64_t n, int ncols, DType ts, const void* src, int64_t lds
     LG_CHECK_LAUNCH();
 }
 
+
+size_t vcycle_small_smem(const Grid3* g, int nl, DType t) {
+    const size_t cs = t == DT_F64 ? 8 : 4;
+    size_t elems = 0;
+    for (int l = 0; l < nl; ++l) elems += 3 * (size_t)g[l].n();
+    return 2 * (size_t)g[nl - 1].n() * sizeof(double) + elems * cs;
+}
+
+void launch_vcycle_small(const Grid3* g, const double* scales, int nl, double omega, int nu_pre, int nu_post,
+                         const double* tables, int ncols, DType t, const void* r, int64_t ldr, void* e,
+                         int64_t lde, cudaStream_t st) {
+    LG_REQUIRE(nl >= 1 && nl <= kFuseMaxLevels, LOBPCG_ERR_ARG, "too many fused levels");
+    SmallLevels L{};
+    L.nl = nl;
+    int off = 0;
+    for (int l = 0; l < nl; ++l) {
+        L.g[l] = g[l];
+        L.s[l] = scales[l];
+        L.off[l] = off;
+        off += 3 * (int)g[l].n();
+    }
+    const size_t smem = vcycle_small_smem(g, nl, t);
+    LG_REQUIRE(smem <= 200 * 1024, LOBPCG_ERR_ARG, "fused V-cycle levels do not fit in shared memory");
+    static bool attr[64][3] = {};
+    int dev = 0;
+    LG_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !attr[dev][t]) {
+        if (t == DT_F64) LG_CUDA(cudaFuncSetAttribute(k_vcycle_small<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        if (t == DT_F32) LG_CUDA(cudaFuncSetAttribute(k_vcycle_small<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        if (t == DT_BF16) LG_CUDA(cudaFuncSetAttribute(k_vcycle_small<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr[dev][t] = true;
+    }
+    switch (t) {
+        case DT_F64: k_vcycle_small<double, double><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const double*)r, ldr, (double*)e, lde); break;
+        case DT_F32: k_vcycle_small<float, float><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const float*)r, ldr, (float*)e, lde); break;
+        case DT_BF16: k_vcycle_small<__nv_bfloat16, float><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const __nv_bfloat16*)r, ldr, (__nv_bfloat16*)e, lde); break;
+    }
+    LG_CHECK_LAUNCH();
+}
 }  // namespace lg

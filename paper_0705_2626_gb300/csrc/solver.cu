@@ -301,6 +301,13 @@ void vcycle(lobpcg_t* h, int l, int b, DType t, const void* r, int64_t ldr, void
         launch_coarse_solve(g, b, t, f64(h->coarse_tab), r, ldr, e, lde, h->stream);
         return;
     }
+    if (n <= kFuseMaxPoints && L - l <= kFuseMaxLevels &&
+        vcycle_small_smem(h->lv.data() + l, L - l, t) <= 200 * 1024) {
+        // the small levels in one kernel (shared memory)
+        launch_vcycle_small(h->lv.data() + l, h->lscale.data() + l, L - l, h->omega, h->nu_pre, h->nu_post,
+                            f64(h->coarse_tab), b, t, r, ldr, e, lde, h->stream);
+        return;
+    }
     const double s = h->lscale[l], w = h->omega, alpha = w / (6.0 * s);
     void* cur = e;
     int64_t ldc = lde;
