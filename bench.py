@@ -291,12 +291,14 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- per-kernel HBM rooflines from the phase events (all m columns active, b = m)
     q = 3 * m
-    kern64 = dict(spmv_step12=hbm_frac(2 * 8 * n * m, ph64["spmv"]),
+    kern64 = dict(residual_step7=hbm_frac(3 * 8 * n * m, ph64["residual"]),
+                  spmv_step12=hbm_frac(2 * 8 * n * m, ph64["spmv"]),
                   vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 8, 8), ph64["precond"]),
                   gram_steps17_23=hbm_frac(2 * q * 8 * n, ph64["gram"]),
                   note="float64 stencil and V-cycle are bound by GB300's float64 pipe (1/64 of float32), "
                        "not by HBM")
-    kernmx = dict(spmv_step12=hbm_frac(2 * 4 * n * m, phmx["spmv"]),
+    kernmx = dict(residual_step7=hbm_frac(3 * 4 * n * m, phmx["residual"]),
+                  spmv_step12=hbm_frac(2 * 4 * n * m, phmx["spmv"]),
                   vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 4, 2), phmx["precond"]),
                   gram_steps17_23=hbm_frac((2 * q + 2 * m) * 4 * n, phmx["gram"]),
                   update_steps25_33=hbm_frac((2 * m + 2 * m + 3 * m) * 4 * n, phmx["update"]))

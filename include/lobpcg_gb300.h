@@ -70,11 +70,12 @@ extern "C" {
 #define LOBPCG_NPHASES         8
 
 /* Phase indices of lobpcg_info.phase_ms. */
-#define LOBPCG_PH_RESIDUAL     0   /* steps 7-8  */
-#define LOBPCG_PH_PRECOND      1   /* step 9     */
-#define LOBPCG_PH_CHOLQR_W     2   /* step 11    */
+#define LOBPCG_PH_RESIDUAL     0   /* steps 7-8 (residuals and their norms) */
+#define LOBPCG_PH_PRECOND      1   /* step 9 (the V-cycle) */
+#define LOBPCG_PH_CHOLQR_W     2   /* step 11; mixed form: with the Gram-Schmidt of W against X */
 #define LOBPCG_PH_SPMV         3   /* step 12    */
-#define LOBPCG_PH_CHOLQR_P     4   /* steps 13-16 */
+#define LOBPCG_PH_CHOLQR_P     4   /* steps 13-16; mixed form: with the Gram-Schmidt of P
+                                      against [X W] and AP_J = A P_J */
 #define LOBPCG_PH_GRAM         5   /* steps 17-23 */
 #define LOBPCG_PH_RR           6   /* step 24    */
 #define LOBPCG_PH_UPDATE       7   /* steps 25-33 */

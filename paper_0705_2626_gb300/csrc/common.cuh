@@ -169,6 +169,8 @@ int g32_chunks(int64_t n);
 void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const float* S1, int w1,
                          const float* V, int b, double* C, double* G, double* part,
                          int64_t part_doubles, unsigned* status, cudaStream_t st);
+// G -= C^T C (G b x b symmetric, C w x b column-major with leading dimension ldc), float64.
+void launch_gram_sub_ctc(int w, int b, const double* C, int ldc, double* G, cudaStream_t st);
 // Residual-form Gram of the mixed form, S = [X W P] (X as hi / lo planes Xh, Xl), T = [R AW AP]
 // (R = AX - X Lambda): float32 tiles for every block but X^T X, double-float tiles for X^T X,
 // then gramA, gramB (q x q, q = m + b + bp) as in launch_gram_mx.

@@ -284,6 +284,17 @@ __global__ void k_part_sum(int rows, int cols, int ldp, int64_t off, int64_t str
     if (sym) out[j + (int64_t)ldo * i] = s;
 }
 
+// G -= C^T C for the b x b matrix G and the w x b matrix C (column-major, ld ldc); one thread
+// per entry.
+__global__ void k_sub_ctc(int w, int b, const double* __restrict__ C, int ldc, double* __restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b * b) return;
+    const int i = e % b, j = e / b;
+    double s = 0.0;
+    for (int k = 0; k < w; ++k) s = fma(C[k + (int64_t)ldc * i], C[k + (int64_t)ldc * j], s);
+    G[i + (int64_t)b * j] -= s;
+}
+
 // ---------------------------------------------------------------- host side
 struct G32Block {
     const float* p;
@@ -397,6 +408,12 @@ void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t
     LG_REQUIRE(r == CUDA_SUCCESS, LOBPCG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
 
+
+void launch_gram_sub_ctc(int w, int b, const double* C, int ldc, double* G, cudaStream_t st) {
+    if (b <= 0 || w <= 0) return;
+    k_sub_ctc<<<(unsigned)ceil_div((int64_t)b * b, 256), 256, 0, st>>>(w, b, C, ldc, G);
+    LG_CHECK_LAUNCH();
+}
 
 int g32_chunks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 512), 2 * kNumSMs)); }
 

@@ -81,14 +81,31 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
 }
 
-// Float32 storage with nx divisible by 4: each thread owns 4 consecutive points of an x-row
-// (one float4) and marches along k, so a point costs about 1.25 load instructions instead of 6.
-// Same arithmetic as the float32 branch above (difference form, neighbours added in the same
-// order).
-template <bool HAS_Z>
+// Float32 or bfloat16 storage with nx divisible by 4: each thread owns 4 consecutive points of an
+// x-row (one 16- or 8-byte vector) and marches along k, so a point costs about 1.25 load
+// instructions instead of 6.  Float32 arithmetic, the difference form of the branch above with
+// the neighbours added in the same order.
+__device__ __forceinline__ float4 ld4v(const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); }
+__device__ __forceinline__ float4 ld4v(const __nv_bfloat16* q) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(q));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+__device__ __forceinline__ void st4v(float* q, const float (&o)[4]) {
+    *reinterpret_cast<float4*>(q) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4v(__nv_bfloat16* q, const float (&o)[4]) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]), hi = __floats2bfloat162_rn(o[2], o[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned*>(&lo);
+    u.y = *reinterpret_cast<const unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(q) = u;
+}
+
+template <typename T, bool HAS_Z>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_stencil_f32v4(Grid3 g, int zchunk, int nzc, float a, float b, const float* __restrict__ x, int64_t ldx,
-                    float c, const float* __restrict__ z, int64_t ldz, float* __restrict__ y, int64_t ldy) {
+    k_stencil_v4(Grid3 g, int zchunk, int nzc, float a, float b, const T* __restrict__ x, int64_t ldx,
+                 float c, const T* __restrict__ z, int64_t ldz, T* __restrict__ y, int64_t ldy) {
     const int nx4 = g.nx >> 2;
     const int i4 = blockIdx.x * kTX + threadIdx.x;
     const int j = blockIdx.y * kTY + threadIdx.y;
@@ -99,23 +116,22 @@ __global__ void __launch_bounds__(kTX* kTY)
     const int k0 = kc * zchunk;
     const int k1 = min(k0 + zchunk, g.nz);
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    const float* xc = x + (int64_t)col * ldx;
-    const float* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
-    float* yc = y + (int64_t)col * ldy;
-    auto ld4 = [](const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); };
+    const T* xc = x + (int64_t)col * ldx;
+    const T* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
+    T* yc = y + (int64_t)col * ldy;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     int64_t p = i0 + sy * (j + (int64_t)g.ny * k0);
-    float4 xm = k0 > 0 ? ld4(xc + p - sz) : zero;
-    float4 x0 = ld4(xc + p);
+    float4 xm = k0 > 0 ? ld4v(xc + p - sz) : zero;
+    float4 x0 = ld4v(xc + p);
     const bool hasl = i0 > 0, hasr = i0 + 4 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
     const float a6 = a + 6.f * b;
     for (int k = k0; k < k1; ++k, p += sz) {
-        const float4 xp = (k + 1 < g.nz) ? ld4(xc + p + sz) : zero;
-        const float l = hasl ? __ldg(xc + p - 1) : 0.f;
-        const float r = hasr ? __ldg(xc + p + 4) : 0.f;
-        const float4 yd = hasd ? ld4(xc + p - sy) : zero;
-        const float4 yu = hasu ? ld4(xc + p + sy) : zero;
-        const float4 zz = HAS_Z ? ld4(zc + p) : zero;
+        const float4 xp = (k + 1 < g.nz) ? ld4v(xc + p + sz) : zero;
+        const float l = hasl ? (float)ld_as(xc + p - 1) : 0.f;
+        const float r = hasr ? (float)ld_as(xc + p + 4) : 0.f;
+        const float4 yd = hasd ? ld4v(xc + p - sy) : zero;
+        const float4 yu = hasu ? ld4v(xc + p + sy) : zero;
+        const float4 zz = HAS_Z ? ld4v(zc + p) : zero;
         const float cx[6] = {l, x0.x, x0.y, x0.z, x0.w, r};
         const float m_[4] = {xm.x, xm.y, xm.z, xm.w}, p_[4] = {xp.x, xp.y, xp.z, xp.w};
         const float d_[4] = {yd.x, yd.y, yd.z, yd.w}, u_[4] = {yu.x, yu.y, yu.z, yu.w};
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(kTX* kTY)
             if (HAS_Z) v = fmaf(c, z_[e], v);
             o[e] = v;
         }
-        *reinterpret_cast<float4*>(yc + p) = make_float4(o[0], o[1], o[2], o[3]);
+        st4v(yc + p, o);
         xm = x0;
         x0 = xp;
     }
@@ -521,16 +537,17 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
     const int zc = zchunk_for(g.nz);
     const int nzc = (int)ceil_div(g.nz, zc);
     dim3 block(kTX, kTY);
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (!std::is_same<T, double>::value) {
+        constexpr uintptr_t al = 4 * sizeof(T);    // one 4-point vector
         if (g.nx % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && (!z || ldz % 4 == 0) &&
-            ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % 16 == 0) {
+            ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % al == 0) {
             dim3 grid4((unsigned)ceil_div(g.nx / 4, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
             if (z)
-                k_stencil_f32v4<true><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const float*)x, ldx,
-                                                               (float)c, (const float*)z, ldz, (float*)y, ldy);
+                k_stencil_v4<T, true><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
+                                                               (float)c, (const T*)z, ldz, (T*)y, ldy);
             else
-                k_stencil_f32v4<false><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const float*)x, ldx,
-                                                                0.f, nullptr, 0, (float*)y, ldy);
+                k_stencil_v4<T, false><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
+                                                                0.f, nullptr, 0, (T*)y, ldy);
             return;
         }
     }

@@ -109,7 +109,7 @@ struct lobpcg_handle {
     int fp64_sweeps = 0;
     double setup_ms = 0.0, solve_ms = 0.0;
     double phase_ms[LOBPCG_NPHASES] = {};
-    cudaEvent_t ev[LOBPCG_NPHASES + 2] = {};
+    cudaEvent_t ev[LOBPCG_NPHASES + 3] = {};   // phase marks, solve start / end, end of the residual
     long long launches_at_start = 0;
 };
 
@@ -386,7 +386,11 @@ void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* 
 // Rayleigh-Ritz step is unchanged; the basis [X W P] becomes well conditioned, which the
 // float32 search directions need (with near-dependent columns the float32 roundings of the Gram
 // matrices would be magnified into spurious Ritz pairs).
-void project_out(lobpcg_t* h, int b, void* V, const void* W) {
+// The second pass also returns G = V^T V of the projected block for its Cholesky step (11 / 15):
+// the pass computes C = [X W]^T V and V^T V before it subtracts [X W] C, and
+// (V - L C)^T (V - L C) = V^T V - C^T C when L = [X W] has orthonormal columns (to float32
+// accuracy; C is at the float32 rounding level in that pass, so the neglected term is ~1e-14).
+void project_out(lobpcg_t* h, int b, void* V, const void* W, double* G) {
     const int64_t n = h->g.n();
     const int m = h->m;
     const int wb = W ? b : 0;
@@ -394,11 +398,12 @@ void project_out(lobpcg_t* h, int b, void* V, const void* W) {
     const float* Wf = static_cast<const float*>(W);
     for (int pass = 0; pass < 2; ++pass) {
         // coefficients [X W]^T V ((m + wb) x b) in gramB, which is free until steps 17-23
-        launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, static_cast<const float*>(V), b, h->gramB, nullptr,
-                            f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+        launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, static_cast<const float*>(V), b, h->gramB,
+                            pass == 1 ? G : nullptr, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
         launch_project32(n, b, static_cast<float*>(V), Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status,
                          h->stream);
     }
+    launch_gram_sub_ctc(m + wb, b, h->gramB, m + wb, G, h->stream);
 }
 
 // V <- V Rinv (steps 11 and 15), in place; skipped on the device if *status & skip.
@@ -627,10 +632,10 @@ void pass_body(lobpcg_t* h) {
     }
     precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
-    if (mixed) project_out(h, b, h->W.p, nullptr);
     tm.mark(1);
-    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J)
-    block_gram(h, b, tw, h->W.p, h->Gsmall);
+    if (mixed) project_out(h, b, h->W.p, nullptr, h->Gsmall);
+    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form has the Gram from its projection)
+    if (!mixed) block_gram(h, b, tw, h->W.p, h->Gsmall);
     launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
     apply_rinv(h, b, tw, h->W.p, ST_W_BREAKDOWN);
     tm.mark(2);
@@ -654,8 +659,8 @@ void pass_body(lobpcg_t* h) {
             Pj = h->Pc.p;
             APj = h->APc.p;
         }
-        if (mixed) project_out(h, b, Pj, h->W.p);
-        block_gram(h, b, tw, Pj, h->Gsmall);
+        if (mixed) project_out(h, b, Pj, h->W.p, h->Gsmall);
+        else block_gram(h, b, tw, Pj, h->Gsmall);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
         apply_rinv(h, b, tw, Pj, ST_W_BREAKDOWN | ST_P_DROPPED);
         if (h->precision == LOBPCG_MIXED) {
@@ -701,6 +706,7 @@ void pass_body(lobpcg_t* h) {
     // step 7 of the next pass
     if (mixed) residual_from_planes(h);
     else residual_into_W(h);
+    if (tm.on) LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 2], st));
     const unsigned stw = fetch_small(h);
     if (h->phase_timing) {
         // events 0..7 bracket phases 1..7 of this pass; the residual phase is the tail
@@ -709,6 +715,9 @@ void pass_body(lobpcg_t* h) {
             LG_CUDA(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
             h->phase_ms[i + 1] += ms;
         }
+        float ms = 0.f;
+        LG_CUDA(cudaEventElapsedTime(&ms, h->ev[7], h->ev[LOBPCG_NPHASES + 2]));
+        h->phase_ms[LOBPCG_PH_RESIDUAL] += ms;
     }
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
     if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
