@@ -109,6 +109,96 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
 }
 
+// The same residual for nx divisible by 4: each thread owns 4 consecutive points of an x-row
+// (float4 loads of both planes); identical arithmetic per point.
+__global__ void __launch_bounds__(kTX* kTY)
+    k_resid_mx4(Grid3 g, int zchunk, int nzc, double scale, const float* __restrict__ Xh,
+                const float* __restrict__ Xl, int64_t ld, const double* __restrict__ lam, float* __restrict__ R,
+                int64_t ldr, double* __restrict__ partial) {
+    const int i4 = blockIdx.x * kTX + threadIdx.x;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / nzc;
+    const int kc = blockIdx.z - col * nzc;
+    const int nblk = gridDim.x * gridDim.y * nzc;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * kc);
+    float sh, sl, lh, ll;
+    split(scale, sh, sl);
+    split(lam[col], lh, ll);
+    float acc = 0.f;
+    if (4 * i4 < g.nx && j < g.ny) {
+        const int i0 = 4 * i4;
+        const int k0 = kc * zchunk;
+        const int k1 = min(k0 + zchunk, g.nz);
+        const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+        const float* xh = Xh + (int64_t)col * ld;
+        const float* xl = Xl + (int64_t)col * ld;
+        float* rc = R + (int64_t)col * ldr;
+        auto l4 = [](const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); };
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t p = i0 + sy * (j + (int64_t)g.ny * k0);
+        float4 mh = z4, ml = z4;
+        if (k0 > 0) { mh = l4(xh + p - sz); ml = l4(xl + p - sz); }
+        float4 ch = l4(xh + p), cl = l4(xl + p);
+        const bool hl = i0 > 0, hr = i0 + 4 < g.nx, hd = j > 0, hu = j + 1 < g.ny;
+        for (int k = k0; k < k1; ++k, p += sz) {
+            float4 ph = z4, pl = z4;
+            if (k + 1 < g.nz) { ph = l4(xh + p + sz); pl = l4(xl + p + sz); }
+            const float4 dh = hd ? l4(xh + p - sy) : z4, dl = hd ? l4(xl + p - sy) : z4;
+            const float4 uh = hu ? l4(xh + p + sy) : z4, ul = hu ? l4(xl + p + sy) : z4;
+            const float lfh = hl ? __ldg(xh + p - 1) : 0.f, lfl = hl ? __ldg(xl + p - 1) : 0.f;
+            const float rth = hr ? __ldg(xh + p + 4) : 0.f, rtl = hr ? __ldg(xl + p + 4) : 0.f;
+            const float chv[6] = {lfh, ch.x, ch.y, ch.z, ch.w, rth};
+            const float clv[6] = {lfl, cl.x, cl.y, cl.z, cl.w, rtl};
+            const float mhv[4] = {mh.x, mh.y, mh.z, mh.w}, mlv[4] = {ml.x, ml.y, ml.z, ml.w};
+            const float phv[4] = {ph.x, ph.y, ph.z, ph.w}, plv[4] = {pl.x, pl.y, pl.z, pl.w};
+            const float dhv[4] = {dh.x, dh.y, dh.z, dh.w}, dlv[4] = {dl.x, dl.y, dl.z, dl.w};
+            const float uhv[4] = {uh.x, uh.y, uh.z, uh.w}, ulv[4] = {ul.x, ul.y, ul.z, ul.w};
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float xh0 = chv[e + 1], xl0 = clv[e + 1];
+                float hi = __fmul_rn(6.f, xh0);
+                float lo = fmaf(6.f, xl0, fmaf(6.f, xh0, -hi));
+                auto sub = [&](float qh, float ql) {
+                    float s, er;
+                    two_sum(hi, -qh, s, er);
+                    hi = s;
+                    lo = __fsub_rn(__fadd_rn(lo, er), ql);
+                };
+                sub(mhv[e], mlv[e]);
+                sub(phv[e], plv[e]);
+                sub(chv[e], clv[e]);            // x-1 (zero outside)
+                sub(chv[e + 2], clv[e + 2]);    // x+1
+                sub(dhv[e], dlv[e]);
+                sub(uhv[e], ulv[e]);
+                const float yh = __fmul_rn(hi, sh);
+                const float ye = fmaf(lo, sh, fmaf(hi, sl, fmaf(hi, sh, -yh)));
+                const float qh = __fmul_rn(lh, xh0);
+                const float qe = fmaf(ll, xh0, fmaf(lh, xl0, fmaf(lh, xh0, -qh)));
+                float s, er;
+                two_sum(yh, -qh, s, er);
+                const float r = __fadd_rn(s, __fadd_rn(er, __fsub_rn(ye, qe)));
+                out[e] = r;
+                acc = fmaf(r, r, acc);
+            }
+            *reinterpret_cast<float4*>(rc + p) = make_float4(out[0], out[1], out[2], out[3]);
+            mh = ch; ml = cl;
+            ch = ph; cl = pl;
+        }
+    }
+    double v = acc;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int t = threadIdx.y * kTX + threadIdx.x;
+    __shared__ double redd[kTX * kTY / 32];
+    if ((t & 31) == 0) redd[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+        double sacc = 0.0;
+        for (int w = 0; w < kTX * kTY / 32; ++w) sacc += redd[w];
+        partial[(int64_t)col * nblk + bid] = sacc;
+    }
+}
+
 __global__ void k_planes_to_f64(int64_t n, int m, const float* __restrict__ Xh, const float* __restrict__ Xl,
                                 int64_t ld, double* __restrict__ X, int64_t ldx) {
     const int c = blockIdx.y;
@@ -118,17 +208,25 @@ __global__ void k_planes_to_f64(int64_t n, int m, const float* __restrict__ Xh, 
 
 }  // namespace
 
+static bool resid_vec4(const Grid3& g) { return g.nx % 4 == 0; }
+
 int resid_mx_blocks(const Grid3& g) {
     const int zc = zchunk_mx(g.nz);
-    return (int)(ceil_div(g.nx, kTX) * ceil_div(g.ny, kTY) * ceil_div(g.nz, zc));
+    const int64_t gx = resid_vec4(g) ? ceil_div(g.nx / 4, kTX) : ceil_div(g.nx, kTX);
+    return (int)(gx * ceil_div(g.ny, kTY) * ceil_div(g.nz, zc));
 }
 
 void launch_resid_mx(const Grid3& g, int m, double scale, const float* Xh, const float* Xl, int64_t ld,
                      const double* lam, float* R, int64_t ldr, double* partial, cudaStream_t st) {
     const int zc = zchunk_mx(g.nz);
     const int nzc = (int)ceil_div(g.nz, zc);
-    dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * m));
-    k_resid_mx<<<grid, dim3(kTX, kTY), 0, st>>>(g, zc, nzc, scale, Xh, Xl, ld, lam, R, ldr, partial);
+    if (resid_vec4(g) && ld % 4 == 0 && ldr % 4 == 0) {
+        dim3 grid((unsigned)ceil_div(g.nx / 4, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * m));
+        k_resid_mx4<<<grid, dim3(kTX, kTY), 0, st>>>(g, zc, nzc, scale, Xh, Xl, ld, lam, R, ldr, partial);
+    } else {
+        dim3 grid((unsigned)ceil_div(g.nx, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * m));
+        k_resid_mx<<<grid, dim3(kTX, kTY), 0, st>>>(g, zc, nzc, scale, Xh, Xl, ld, lam, R, ldr, partial);
+    }
     LG_CHECK_LAUNCH();
 }
 
