@@ -149,6 +149,28 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre,
  * per-phase device timing (0/1; adds event records inside each iteration). */
 int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timing);
 
+/* Engine of the float32 Gram products of the mixed form (steps 11, 15, 17-23;
+ * the double-float X^T X block is unaffected):
+ *   LOBPCG_ENGINE_TENSOR: tcgen05 tensor-core MMAs on 3 x TF32 splits (hi*hi +
+ *     hi*lo + lo*hi, about 2^-21 relative per product), float32 accumulation
+ *     in tensor memory over at most 128 grid points (the tensor cores round it
+ *     toward zero: about 1e-6 relative to |s_i| |s_j| when the stacked blocks
+ *     have at most 128 columns, 3e-6 up to 192), compensated float32 sums of
+ *     those, float64 chunk sums.  Used whenever the stacked blocks fit (each
+ *     block padded to a multiple of 8 columns, at most 192 in all, the left
+ *     operands within the first 128); otherwise the SIMT engine runs.
+ *   LOBPCG_ENGINE_SIMT: float32 products with compensated float32 sums on the
+ *     CUDA cores (about 2^-24 relative per product).
+ *   LOBPCG_ENGINE_AUTO (default): the tensor cores for stacks of more than 64
+ *     columns (the residual-form Gram), the SIMT engine below that.  A tensor
+ *     core MMA costs about the same for any N <= 256 on GB300, so the tensor
+ *     form pays off only for wide stacks.
+ * The float64 form ignores it.  Returns ERR_ARG for an unknown engine. */
+#define LOBPCG_ENGINE_AUTO     0
+#define LOBPCG_ENGINE_SIMT     1
+#define LOBPCG_ENGINE_TENSOR   2
+int lobpcg_set_gram_engine(lobpcg_t* h, int engine);
+
 /* Supply the initial block X0 (Algorithm input X): n-by-m, column-major, leading
  * dimension ldx, copied into the handle.  on_host = 1: X0 is host memory;
  * 0: device memory.  Used by the next lobpcg_solve / lobpcg_begin with the same

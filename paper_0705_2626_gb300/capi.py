@@ -23,6 +23,7 @@ LAPLACE7, VARCOEF7 = 0, 1
 PRECOND_NONE, PRECOND_GMG = 0, 1
 TOL_RELATIVE, TOL_ABSOLUTE = 0, 1
 GRAM_EXPLICIT, GRAM_PAPER = 0, 1
+ENGINE_AUTO, ENGINE_SIMT, ENGINE_TENSOR = 0, 1, 2
 MAX_M = 32
 NPHASES = 8
 PHASE_NAMES = ["residual", "precond", "cholqr_w", "spmv", "cholqr_p", "gram", "rayleigh_ritz", "update"]
@@ -47,6 +48,7 @@ _SIGNATURES = {
     "lobpcg_set_operator": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double, c_void_p]),
     "lobpcg_set_preconditioner": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double]),
     "lobpcg_set_options": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "lobpcg_set_gram_engine": (c_int, [c_void_p, c_int]),
     "lobpcg_set_initial": (c_int, [c_void_p, c_void_p, c_int, c_int64, c_int]),
     "lobpcg_solve": (c_int, [c_void_p, c_int, c_double, c_int, c_uint64, ctypes.POINTER(Info)]),
     "lobpcg_begin": (c_int, [c_void_p, c_int, c_double, c_uint64]),
@@ -116,6 +118,10 @@ def lobpcg_set_preconditioner(h, kind, levels, nu_pre, nu_post, omega):
 
 def lobpcg_set_options(h, tol_mode, gram_mode, phase_timing):
     return _call("lobpcg_set_options", h, tol_mode, gram_mode, phase_timing)
+
+
+def lobpcg_set_gram_engine(h, engine):
+    return _call("lobpcg_set_gram_engine", h, engine)
 
 
 def lobpcg_set_initial(h, X0, m, ldx, on_host):

@@ -165,19 +165,22 @@ void launch_gram_finalize_mx(int q, int m, int b, int bp, int nparts, const doub
 // A kernel whose bounded wait gives up sets ST_TIMEOUT in *status.
 int g32_chunks(int64_t n);
 // C = [S0 S1]^T V ((w0 + w1) x b, column-major, ld w0 + w1) and, if G != null, G = V^T V
-// (b x b, symmetric): float32 products, compensated float32 sums, float64 chunk sums.
+// (b x b, symmetric), float64 chunk sums of per-chunk float32 sums.  tc (GramTc): whether the
+// tensor cores (3 x TF32 products, k_gram_tc.cu) may run them, else float32 products with
+// compensated sums on the SIMT pipes.
 void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const float* S1, int w1,
                          const float* V, int b, double* C, double* G, double* part,
-                         int64_t part_doubles, unsigned* status, cudaStream_t st);
+                         int64_t part_doubles, unsigned* status, int tc, cudaStream_t st);
 // G -= C^T C (G b x b symmetric, C w x b column-major with leading dimension ldc), float64.
 void launch_gram_sub_ctc(int w, int b, const double* C, int ldc, double* G, cudaStream_t st);
 // Residual-form Gram of the mixed form, S = [X W P] (X as hi / lo planes Xh, Xl), T = [R AW AP]
-// (R = AX - X Lambda): float32 tiles for every block but X^T X, double-float tiles for X^T X,
-// then gramA, gramB (q x q, q = m + b + bp) as in launch_gram_mx.
+// (R = AX - X Lambda): float32 products for every block but X^T X (engine as in
+// launch_gram32_cross), double-float tiles for X^T X, then gramA, gramB
+// (q x q, q = m + b + bp).
 void launch_gram_mx2(int64_t n, int64_t ld, const float* Xh, const float* Xl, const float* W,
                      const float* P, const float* R, const float* AW, const float* AP, int m, int b,
                      int bp, double* part, int64_t part_doubles, const double* lam, double* gramA,
-                     double* gramB, unsigned* status, cudaStream_t st);
+                     double* gramB, unsigned* status, int tc, cudaStream_t st);
 // ---------------------------------------------------------------- mixed form, X as planes
 // (k_mixed.cu).  X = Xh + Xl (float32 hi / lo planes, ld divisible by 4).
 // R = A X - X diag(lam) (double-float stencil, R float32) for m columns, and per-block sums of

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gram_out.cuh"
 #include "tma.cuh"
 
 namespace lg {
@@ -39,19 +40,6 @@ constexpr int kG32MaxBlocks = 6;
 constexpr int kG32MaxTiles = 640;
 constexpr int kG32SmemBudget = 200 * 1024;
 constexpr int kG32Header = 128;               // mbarriers in front of the stage buffers
-
-enum G32Mode : int { G32_ALL = 0, G32_UPPER = 1, G32_MXA = 2, G32_MXB = 3 };
-
-// One output matrix: entry (i, j) = column (lbase + i) . column (rbase + j) of the staged
-// columns, stored at part[chunk * part_stride + off + i + ld * j] when `need` holds.
-struct G32Out {
-    int64_t off;
-    int ld;
-    int lbase, rbase;
-    int rows, cols;
-    int mode;
-    int w0, w1;       // widths of the X and W blocks (mixed-form predicates)
-};
 
 struct G32Args {
     CUtensorMap map[kG32MaxBlocks];
@@ -70,21 +58,6 @@ struct G32Args {
     uint16_t ti[kG32MaxTiles], tj[kG32MaxTiles];
     uint8_t to[kG32MaxTiles];
 };
-
-__host__ __device__ inline int blk3(int i, int w0, int w1) { return i < w0 ? 0 : (i < w0 + w1 ? 1 : 2); }
-
-__host__ __device__ inline bool g32_need(const G32Out& o, int i, int j) {
-    if (i < 0 || j < 0 || i >= o.rows || j >= o.cols) return false;
-    switch (o.mode) {
-        case G32_UPPER: return i <= j;
-        // S^T T of the residual form: every row against an X column, and the upper block
-        // triangle of the W / P part (diagonal blocks in full)
-        case G32_MXA: return j < o.w0 || (i >= o.w0 && blk3(i, o.w0, o.w1) <= blk3(j, o.w0, o.w1));
-        // S^T S upper triangle outside the X^T X block (that block is double-float)
-        case G32_MXB: return i <= j && j >= o.w0;
-        default: return true;
-    }
-}
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
@@ -296,12 +269,6 @@ __global__ void k_sub_ctc(int w, int b, const double* __restrict__ C, int ldc, d
 }
 
 // ---------------------------------------------------------------- host side
-struct G32Block {
-    const float* p;
-    int w;
-    int coff;
-};
-
 // Tiles of TI x TJ staged columns covering every needed entry of the outputs.
 void build_tiles(G32Args& a, int TI, int TJ) {
     a.ntiles = 0;
@@ -384,7 +351,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 }  // namespace
 
-void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t ld, int box_rows) {
+void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t ld, int box_rows, bool swizzle128) {
     std::call_once(g_encode_once, [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
@@ -402,8 +369,10 @@ void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t
     const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
     const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)w};
     const cuuint32_t es[2] = {1, 1};
+    LG_REQUIRE(!swizzle128 || box_rows * sizeof(float) == 128, LOBPCG_ERR_ARG, "128-byte swizzle needs 32-row boxes");
     const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box,
-                                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     LG_REQUIRE(r == CUDA_SUCCESS, LOBPCG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
@@ -419,7 +388,7 @@ int g32_chunks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(c
 
 void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const float* S1, int w1, const float* V,
                          int b, double* C, double* G, double* part, int64_t part_doubles, unsigned* status,
-                         cudaStream_t st) {
+                         int tc, cudaStream_t st) {
     const int wl = w0 + w1;
     if (b <= 0 || (wl == 0 && !G)) return;
     const int vb = ((wl + 7) / 8) * 8;
@@ -441,7 +410,8 @@ void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const f
     const int nchunks = g32_chunks(n);
     a.part_stride = off;
     LG_REQUIRE(nchunks * off <= part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
-    g32_launch<false>(a, n, ld, blk, 3, Q, nchunks, part, status, st);
+    if (!launch_gram_tc(blk, 3, a.out, a.nout, off, n, ld, nchunks, part, status, tc, st))
+        g32_launch<false>(a, n, ld, blk, 3, Q, nchunks, part, status, st);
     if (wl > 0) part_sum(wl, b, wl, 0, off, nchunks, part, C, wl, false, st);
     if (G) part_sum(b, b, b, goff, off, nchunks, part, G, b, true, st);
 }
@@ -449,7 +419,7 @@ void launch_gram32_cross(int64_t n, int64_t ld, const float* S0, int w0, const f
 void launch_gram_mx2(int64_t n, int64_t ld, const float* Xh, const float* Xl, const float* W, const float* P,
                      const float* R, const float* AW, const float* AP, int m, int b, int bp, double* part,
                      int64_t part_doubles, const double* lam, double* gramA, double* gramB, unsigned* status,
-                     cudaStream_t st) {
+                     int tc, cudaStream_t st) {
     const int q = m + b + bp;
     const int qp = ((q + 7) / 8) * 8;
     const int nchunks = g32_chunks(n);
@@ -464,7 +434,8 @@ void launch_gram_mx2(int64_t n, int64_t ld, const float* Xh, const float* Xl, co
         a.out[0] = G32Out{0, q, 0, qp, q, q, G32_MXA, m, b};
         a.out[1] = G32Out{q2, q, 0, 0, q, q, G32_MXB, m, b};
         a.part_stride = 2 * q2;
-        g32_launch<false>(a, n, ld, blk, 6, 2 * qp, nchunks, part, status, st);
+        if (!launch_gram_tc(blk, 6, a.out, a.nout, a.part_stride, n, ld, nchunks, part, status, tc, st))
+            g32_launch<false>(a, n, ld, blk, 6, 2 * qp, nchunks, part, status, st);
     }
     // double-float X^T X: hi plane at 0, lo plane at mp
     {

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gram_out.cuh"
 
 using namespace lg;
 
@@ -74,6 +75,7 @@ struct lobpcg_handle {
     Buf vc_inv;
     // options
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
+    int gram_engine = LOBPCG_ENGINE_AUTO;       // float32 Grams of the mixed form
 
     // workspace for a block of wm columns
     int wm = 0;
@@ -381,6 +383,11 @@ void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* 
     launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
 }
 
+int use_tc(const lobpcg_t* h) {
+    return h->gram_engine == LOBPCG_ENGINE_TENSOR ? GRAM_TC_ALWAYS
+                                                  : (h->gram_engine == LOBPCG_ENGINE_AUTO ? GRAM_TC_WIDE : GRAM_TC_NEVER);
+}
+
 // Mixed form: two passes of block Gram-Schmidt of V (b float32 columns) against X (m float64
 // columns) and, if W != null, against W (b float32 columns).  The trial subspace of the
 // Rayleigh-Ritz step is unchanged; the basis [X W P] becomes well conditioned, which the
@@ -399,7 +406,8 @@ void project_out(lobpcg_t* h, int b, void* V, const void* W, double* G) {
     for (int pass = 0; pass < 2; ++pass) {
         // coefficients [X W]^T V ((m + wb) x b) in gramB, which is free until steps 17-23
         launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, static_cast<const float*>(V), b, h->gramB,
-                            pass == 1 ? G : nullptr, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+                            pass == 1 ? G : nullptr, f64(h->part), (int64_t)h->part_doubles, h->status, use_tc(h),
+                            h->stream);
         launch_project32(n, b, static_cast<float*>(V), Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status,
                          h->stream);
     }
@@ -418,7 +426,7 @@ void apply_rinv(lobpcg_t* h, int b, DType t, void* V, unsigned skip) {
 void block_gram(lobpcg_t* h, int b, DType t, const void* V, double* G) {
     if (t == DT_F32) {
         launch_gram32_cross(h->g.n(), h->ld, nullptr, 0, nullptr, 0, static_cast<const float*>(V), b, nullptr, G,
-                            f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+                            f64(h->part), (int64_t)h->part_doubles, h->status, use_tc(h), h->stream);
     } else {
         const Blocks3 S = blocks(V, b, t, nullptr, 0, nullptr, 0, t, h->ld);
         gram(h, S, nullptr, h->gramA, G, nullptr);
@@ -680,7 +688,8 @@ void pass_body(lobpcg_t* h) {
     if (mixed) {
         auto F = [](const void* p) { return static_cast<const float*>(p); };
         launch_gram_mx2(n, ld, F(h->Xh.p), F(h->Xl.p), F(h->W.p), F(Pj), F(h->R.p), F(h->AW.p), F(APj), m, b,
-                        use_p ? b : 0, f64(h->part), (int64_t)h->part_doubles, h->lam, h->gramA, h->gramB, h->status, st);
+                        use_p ? b : 0, f64(h->part), (int64_t)h->part_doubles, h->lam, h->gramA, h->gramB, h->status,
+                        use_tc(h), st);
     } else {
         gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
     }
@@ -991,6 +1000,16 @@ int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timin
     });
 }
 
+int lobpcg_set_gram_engine(lobpcg_t* h, int engine) {
+    return guarded(h, [&] {
+        LG_REQUIRE(engine == LOBPCG_ENGINE_AUTO || engine == LOBPCG_ENGINE_TENSOR || engine == LOBPCG_ENGINE_SIMT,
+                   LOBPCG_ERR_ARG,
+                   "unknown Gram engine");
+        h->gram_engine = engine;
+        return LOBPCG_OK;
+    });
+}
+
 int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on_host) {
     return guarded(h, [&] {
         require_op(h);
@@ -1209,7 +1228,7 @@ int lobpcg_op_gram_f32(lobpcg_t* h, const float* S0, int w0, const float* S1, in
         cudaStream_t st = h->stream;
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
         launch_gram32_cross(n, ld, S0, w0, S1, w1, V, b, (w0 + w1) ? C : nullptr, G, f64(h->part),
-                            (int64_t)h->part_doubles, h->status, st);
+                            (int64_t)h->part_doubles, h->status, use_tc(h), st);
         unsigned stw = 0;
         LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         LG_CUDA(cudaStreamSynchronize(st));
@@ -1232,7 +1251,7 @@ int lobpcg_op_gram_residual(lobpcg_t* h, const float* Xh, const float* Xl, const
         cudaStream_t st = h->stream;
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
         launch_gram_mx2(n, ld, Xh, Xl, W, bp ? P : W, R, AW, bp ? AP : AW, m, b, bp, f64(h->part),
-                        (int64_t)h->part_doubles, lambda, gramA, gramB, h->status, st);
+                        (int64_t)h->part_doubles, lambda, gramA, gramB, h->status, use_tc(h), st);
         unsigned stw = 0;
         LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         LG_CUDA(cudaStreamSynchronize(st));

@@ -7,8 +7,12 @@
 namespace lg {
 
 // Column blocks of float32 (n rows, w columns, leading dimension ld divisible by 4, 16-byte
-// aligned) as a 2-D tensor map with boxes of box_rows x w; rows beyond n read as zeros.
-void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t ld, int box_rows);
+// aligned) as a 2-D tensor map with boxes of box_rows x w; rows beyond n read as zeros.  With
+// swizzle128 (box_rows = 32: one 128-byte line per column) the box lands in shared memory in the
+// 128-byte swizzled layout that the tensor cores read (16-byte chunk c of line r stored at chunk
+// c ^ (r mod 8)).
+void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t ld, int box_rows,
+                     bool swizzle128 = false);
 
 namespace {
 

@@ -58,10 +58,12 @@ class Solver:
 
     def __init__(self, dims, scale=None, precond="gmg", levels=None, nu=2, omega=2.0 / 3.0,
                  device=0, stream=None, tol_mode="relative", gram="explicit", phase_timing=False,
-                 torch_allocator=True, precision="fp64", kappa=None):
+                 torch_allocator=True, precision="fp64", kappa=None, gram_engine="auto"):
         """kappa: face coefficients of the variable-coefficient operator -div(kappa grad u) (unit
         spacing; layout of paper_0705_2626_gb300.fields), a float64 numpy array or torch tensor;
-        None selects the constant-coefficient Laplacian."""
+        None selects the constant-coefficient Laplacian.  gram_engine: "auto" (tensor cores for wide
+        stacks), "tensor" (tcgen05, 3 x TF32, whenever the blocks fit) or "simt" for the float32 Gram
+        products of the mixed form."""
         if precision not in ("fp64", "mixed"):
             raise ValueError(f"precision must be 'fp64' or 'mixed', not {precision!r}")
         self.precision = precision
@@ -105,6 +107,10 @@ class Solver:
         _check(capi.lobpcg_set_options(h, capi.TOL_RELATIVE if tol_mode == "relative" else capi.TOL_ABSOLUTE,
                                        capi.GRAM_EXPLICIT if gram == "explicit" else capi.GRAM_PAPER,
                                        1 if phase_timing else 0), h)
+        engines = {"auto": capi.ENGINE_AUTO, "simt": capi.ENGINE_SIMT, "tensor": capi.ENGINE_TENSOR}
+        if gram_engine not in engines:
+            raise ValueError(f"gram_engine must be one of {sorted(engines)}, not {gram_engine!r}")
+        _check(capi.lobpcg_set_gram_engine(h, engines[gram_engine]), h)
         self.m = None
         self.info = capi.Info()
 

@@ -1,11 +1,16 @@
-"""Float32 Gram kernels of the mixed form (TMA-staged, k_gram32.cu) through the C ABI.
+"""Float32 Gram kernels of the mixed form through the C ABI, both engines: the SIMT tiles
+(k_gram32.cu) and the tcgen05 tensor-core form (k_gram_tc.cu).
 
 Inputs are float32 blocks; the expected values are float64 products of the same float32 values
 (the plain definitions S^T V, V^T V) and, for the residual form, the oracle's Gram matrices of
 steps 17-23 (upper block triangle, symmetrised diagonal blocks) of the basis [X W P] with
 X = Xh + Xl.  The residual form equals them in exact arithmetic; the bounds allow the float32
-rounding of the inputs R, AW, AP and the float32 sums (1e-6 of |s_i| |t_j|), and 1e-12 for the
-double-float X^T X block.
+rounding of the inputs R, AW, AP and the arithmetic of the engine, relative to |s_i| |t_j|:
+  SIMT: float32 products, compensated sums: 1e-6;
+  tensor cores: 3 x TF32 products (2^-20) and float32 accumulation in tensor memory that rounds
+  toward zero at each of the at most 96 MMA steps of a 256-point chunk (96 * 2^-23 of the
+  chunk's sum of |s_k t_k|): 1.3e-5;
+and 1e-12 for the double-float X^T X block (same kernel under both engines).
 """
 import os
 import sys
@@ -23,6 +28,8 @@ from paper_0705_2626_gb300.solver import Solver  # noqa: E402
 from tests.gpu_util import ptr  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+ENGINE_TOL = {"simt": 1e-6, "tensor": 1.3e-5}
 
 
 def dev32(X, ld):
@@ -45,8 +52,10 @@ def ld_for(n):
                                           ((40, 36, 34), 16, 16, 16), ((128, 128, 128), 16, 16, 16),
                                           ((20, 20, 20), 32, 32, 32), ((7, 7, 7), 1, 0, 1)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
-def test_gram_f32_cross_and_vtv(dims, w0, w1, b):
-    s = Solver(dims, precond="none")
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_gram_f32_cross_and_vtv(dims, w0, w1, b, engine):
+    tol = ENGINE_TOL[engine]
+    s = Solver(dims, precond="none", gram_engine=engine)
     n, ld = s.n, ld_for(s.n)
     g = np.random.default_rng(11)
     S = f32(g.standard_normal((n, w0 + w1)) * g.uniform(0.1, 10, w0 + w1)[None, :])
@@ -58,8 +67,8 @@ def test_gram_f32_cross_and_vtv(dims, w0, w1, b):
     assert rc == capi.OK, capi.lobpcg_last_error(s.h)
     Cg, Gg = C.cpu().numpy().T, G.cpu().numpy().T
     nS, nV = np.linalg.norm(S, axis=0), np.linalg.norm(V, axis=0)
-    assert np.all(np.abs(Cg - S.T @ V) <= 1e-6 * np.outer(nS, nV))
-    assert np.all(np.abs(Gg - V.T @ V) <= 1e-6 * np.outer(nV, nV))
+    assert np.all(np.abs(Cg - S.T @ V) <= tol * np.outer(nS, nV))
+    assert np.all(np.abs(Gg - V.T @ V) <= tol * np.outer(nV, nV))
     assert np.array_equal(Gg, Gg.T)
     s.close()
 
@@ -93,8 +102,10 @@ def residual_form_inputs(dims, m, b, bp, seed, near=False):
                                               ((128, 128, 128), 16, 16, 16, True), ((40, 40, 40), 32, 32, 32, False),
                                               ((9, 9, 9), 1, 1, 1, False)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
-def test_gram_residual_form_matches_oracle_gram(dims, m, b, bp, near):
-    s = Solver(dims, precond="none")
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_gram_residual_form_matches_oracle_gram(dims, m, b, bp, near, engine):
+    tol = ENGINE_TOL[engine]
+    s = Solver(dims, precond="none", gram_engine=engine)
     d = residual_form_inputs(dims, m, b, bp, seed=3, near=near)
     n, ld, q = d["n"], ld_for(d["n"]), m + b + bp
     blk = {k: dev32(d[k], ld) for k in ("Xh", "Xl", "W", "R", "AW")}
@@ -116,11 +127,11 @@ def test_gram_residual_form_matches_oracle_gram(dims, m, b, bp, near):
     nS, nT = np.linalg.norm(S, axis=0), np.linalg.norm(T, axis=0)
     lamq = np.concatenate([d["lam"], np.zeros(q - m)])
     # gramB: double-float X^T X, float32 elsewhere
-    bound_b = 1e-6 * np.outer(nS, nS)
+    bound_b = tol * np.outer(nS, nS)
     bound_b[:m, :m] = 1e-12 * np.outer(nS[:m], nS[:m])
     assert np.all(np.abs(GB - wantB) <= bound_b)
     # gramA: the float32 part scales with |s_i| |t_j|; the Lambda X^T S part with the gramB error
-    bound_a = 1e-6 * (np.outer(nS, nT) + np.outer(nT, nS)) + np.abs(lamq)[:, None] * bound_b + \
+    bound_a = tol * (np.outer(nS, nT) + np.outer(nT, nS)) + np.abs(lamq)[:, None] * bound_b + \
         np.abs(lamq)[None, :] * bound_b
     assert np.all(np.abs(GA - wantA) <= bound_a)
     assert np.array_equal(GA, GA.T) and np.array_equal(GB, GB.T)

@@ -41,9 +41,10 @@ def complete_clusters(dims, scale, exact, m):
 # nx = 42 is not a multiple of 4: the per-point residual and stencil kernels instead of the
 # float4 ones
 @pytest.mark.parametrize("dims,scale,m,levels", [((40, 36, 34), None, 6, 3), ((42, 36, 34), None, 6, 3), ((48, 48, 48), None, 8, 4)])
-def test_mixed_matches_fp64_oracle(dims, scale, m, levels):
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_mixed_matches_fp64_oracle(dims, scale, m, levels, engine):
     tol = 1e-8
-    s = Solver(dims, scale=scale, levels=levels, precision="mixed")
+    s = Solver(dims, scale=scale, levels=levels, precision="mixed", gram_engine=engine)
     out = s.solve(m, tol=tol, maxit=200, seed=2)
     ref = oracle_run(dims, s.scale, m, tol, 200, levels)
     assert out["status_name"] == "ok", out
@@ -60,10 +61,11 @@ def test_mixed_matches_fp64_oracle(dims, scale, m, levels):
     s.close()
 
 
-def test_mixed_c2_full_size():
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_mixed_c2_full_size(engine):
     """128^3 (2,097,152 unknowns), m = 16, 6-level V-cycle: the bench workload in mixed form."""
     dims, m = (128, 128, 128), 16
-    s = Solver(dims, levels=6, precision="mixed")
+    s = Solver(dims, levels=6, precision="mixed", gram_engine=engine)
     out = s.solve(m, tol=1e-8, maxit=200, seed=2)
     scale = laplace.default_scale(dims)
     exact = laplace.exact_eigenvalues(dims, scale, m)
