@@ -3,14 +3,16 @@
 // memory (TMEM).
 //
 // The column blocks of one launch are stacked as the lines of a tile: block b occupies lines
-// trow[b] .. trow[b] + w[b] - 1 (trow a multiple of 8, unused lines zero), each line holding the
-// 32 consecutive grid points of one stage as one 128-byte row in the 128-byte swizzled layout
-// written by the TMA copy; L = the stacked lines rounded up to 16.
+// trow[b] .. trow[b] + w[b] - 1 (trow a multiple of 8, unused lines zero), each line holding 32
+// consecutive grid points as one 128-byte row in the 128-byte swizzled layout written by the TMA
+// copy; L = the stacked lines rounded up to 16.  A pipeline stage holds kTcAtoms such tiles (64
+// points), so that the fixed costs of a stage (barrier hand-offs, commits) are shared by 8 MMAs.
 //
-// Arithmetic (3 x TF32): the tensor cores read a float32 operand as TF32 (its top 19 bits).  Each
-// value a is split in shared memory into hi = a with the low 13 mantissa bits cleared and
-// lo = a - hi (exact), and the products are hi*hi + hi*lo + lo*hi; the dropped lo*lo term and
-// the TF32 view of lo leave about 2^-21 relative per product.  Two ways to issue them:
+// Arithmetic (3 x TF32): the tensor cores read a float32 operand as TF32 by dropping its low 13
+// mantissa bits (truncation: writing the truncated values back gives bit-identical results), so
+// the copy as it landed serves as hi = a with those bits cleared, and the workers store only
+// lo = a - hi (exact).  The products are hi*hi + hi*lo + lo*hi; the dropped lo*lo term and the
+// TF32 view of lo leave about 2^-21 relative per product.  Two ways to issue them:
 //
 //  * symmetric form (L <= 128): the lo lines follow the hi lines in the same tile, and one MMA
 //    per 8 points, M = 128 (A = lines 0..127) by N = 2L (B = the L hi lines, then the L lo
@@ -23,7 +25,7 @@
 //    one accumulator.
 //
 // The tensor cores keep D in float32 and round each MMA's sum toward zero, so the accumulation
-// in TMEM is kept short: D is reset every kChunkStages stages (128 points) -- 16 MMA steps on
+// in TMEM is kept short: D is reset every 128 points (kChunkStages stages) -- 16 MMA steps on
 // the dominant hi*hi sum in the symmetric form (the cross products sit in their own columns,
 // where the rounding is relative to a 2^-11 smaller sum), 48 in the three-product form.  Worker
 // threads read the accumulators with tcgen05.ld and add them into Kahan-compensated float32
@@ -32,8 +34,9 @@
 //
 // Warp roles (448 threads, one block per SM): warp 0 issues the TMA copies into a ring of
 // stages; warp 1 owns the TMEM allocation and one of its threads issues the MMAs and commits
-// them to mbarriers; warps 2..13 split each landed stage into hi / lo lines and drain the
-// accumulators.  Two accumulator sets alternate, so the MMAs of one chunk run while the previous
+// them to mbarriers; warps 2..13 write the lo lines of each landed stage and drain the
+// accumulators.  Shared-memory bandwidth bounds the kernel: per 32 points the copy writes, the
+// split reads and writes, and the MMAs read A (128 lines) and B (2L lines) from shared memory.  Two accumulator sets alternate, so the MMAs of one chunk run while the previous
 // chunk is drained; the workers drain a finished chunk between stages as soon as its MMAs have
 // completed.  Every wait is bounded (status bit ST_TIMEOUT).
 #include <cuda.h>
@@ -56,8 +59,9 @@ constexpr int kTcColGroups = kTcWorkWarps / 4;   // workers sharing one TMEM lan
 constexpr int kTcMaxL = 192;
 constexpr int kTcSymMaxL = 128;
 constexpr int kTcMaxBlocks = 6;
-constexpr int kTcStagePts = 32;                   // one 128-byte line per column and stage
-constexpr int kChunkStages = 4;
+constexpr int kTcAtoms = 2;                       // 128-byte swizzle atoms (32 points each) per stage
+constexpr int kTcStagePts = 32 * kTcAtoms;
+constexpr int kChunkStages = 2;                   // accumulator reset every 128 points
 constexpr int kTcSmemBudget = 200 * 1024;
 constexpr int kTcCols = 512;                      // TMEM columns: two accumulator sets of 256
 constexpr int kWorkerBarrier = 1;                 // named barrier of the worker warps
@@ -111,11 +115,22 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
     return done != 0;
 }
 
-// Bounded wait that also gives up as soon as another role has flagged a failure.
+// Bounded wait that also gives up as soon as another role has flagged a failure.  The worker
+// warps sleep in try_wait; the single-thread TMA and MMA roles poll with test_wait, which reacts
+// to the phase change sooner.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
 #pragma unroll 1
     for (int it = 0; it < kSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool mbar_poll_or_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag) {
+#pragma unroll 1
+    for (int it = 0; it < 16 * kSpinLimit; ++it) {
+        if (mbar_test(bar, parity)) return true;
         if (*abort_flag) return false;
     }
     return false;
@@ -176,7 +191,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     // swizzled operand tiles must start on a 1024-byte boundary
     unsigned char* smem = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
-    const int stage_bytes = a.stage_lines * 128;
+    const int atom_bytes = a.stage_lines * 128;                  // one 32-point tile
+    const int stage_bytes = kTcAtoms * atom_bytes;
     const int lo_bytes = a.lo_lines * 128;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.nstage * stage_bytes);
     uint64_t* ready = full + a.nstage;
@@ -255,29 +271,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int issued = 0;
-            for (int t = 0; t < nst; ++t) {
-                const int s = t % a.nstage, u = t / a.nstage;
-                if (t >= a.nstage && !mbar_wait_or_abort(&empty[s], (unsigned)((u - 1) & 1), abort_flag)) {
+            for (int t = 0, s = 0, u = 0; t < nst; ++t) {
+                if (t >= a.nstage && !mbar_poll_or_abort(&empty[s], (unsigned)((u - 1) & 1), abort_flag)) {
                     fail();
                     break;
                 }
-                unsigned char* hi = smem + (size_t)s * stage_bytes;
+                unsigned char* st_base = smem + (size_t)s * stage_bytes;
                 mbar_expect_tx(&full[s], a.tx);
-                for (int b = 0; b < a.nblk; ++b)
-                    tma_load_2d(hi + a.trow[b] * 128, &a.map[b], (int)(r0 + (int64_t)t * kTcStagePts), 0, &full[s]);
+                for (int at = 0; at < kTcAtoms; ++at)
+                    for (int b = 0; b < a.nblk; ++b)
+                        tma_load_2d(st_base + at * atom_bytes + a.trow[b] * 128, &a.map[b],
+                                    (int)(r0 + (int64_t)t * kTcStagePts + 32 * at), 0, &full[s]);
                 issued = t + 1;
+                if (++s == a.nstage) {
+                    s = 0;
+                    ++u;
+                }
             }
             *issued_out = issued;
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tf32_idesc(128, SYM ? 2 * a.L : a.L);
-            for (int t = 0; t < nst; ++t) {
-                const int s = t % a.nstage, u = t / a.nstage;
+            const uint32_t ring = smem_addr(smem);
+            for (int t = 0, s = 0, u = 0; t < nst; ++t) {
                 const int c = t / kChunkStages;
                 const bool first = t % kChunkStages == 0;
                 if (first && c >= 2) {
-                    if (!mbar_wait_or_abort(&accempty[c & 1], (unsigned)(((c - 2) >> 1) & 1), abort_flag)) {
+                    if (!mbar_poll_or_abort(&accempty[c & 1], (unsigned)(((c - 2) >> 1) & 1), abort_flag)) {
                         fail();
                         break;
                     }
@@ -285,28 +306,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 // the split's writes reach the tensor cores' (async) proxy through the workers'
                 // fence.proxy.async before their arrival on ready[s]
-                if (!mbar_wait_or_abort(&ready[s], (unsigned)(u & 1), abort_flag)) {
+                if (!mbar_poll_or_abort(&ready[s], (unsigned)(u & 1), abort_flag)) {
                     fail();
                     break;
                 }
                 const uint32_t d = tmem + (uint32_t)((c & 1) * kSet);
-                const uint32_t hi = smem_addr(smem + (size_t)s * stage_bytes);
-                const uint32_t lo = hi + (uint32_t)lo_bytes;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {                    // 8 points (32 bytes) per MMA
-                    const uint64_t dh = sw128_desc(hi + 32u * kk);
-                    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                    if constexpr (SYM) {
-                        mma_tf32(d, dh, dh, idesc, acc);            // B = hi lines then lo lines
-                    } else {
-                        const uint64_t dl = sw128_desc(lo + 32u * kk);
-                        mma_tf32(d, dh, dh, idesc, acc);
-                        mma_tf32(d, dh, dl, idesc, 1u);
-                        mma_tf32(d, dl, dh, idesc, 1u);
+                for (int at = 0; at < kTcAtoms; ++at) {
+                    const uint32_t hi = ring + (uint32_t)(s * stage_bytes + at * atom_bytes);
+                    const uint32_t lo = hi + (uint32_t)lo_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {                // 8 points (32 bytes) per MMA
+                        const uint64_t dh = sw128_desc(hi + 32u * kk);
+                        const uint32_t acc = (first && at == 0 && kk == 0) ? 0u : 1u;
+                        if constexpr (SYM) {
+                            mma_tf32(d, dh, dh, idesc, acc);        // B = hi lines then lo lines
+                        } else {
+                            const uint64_t dl = sw128_desc(lo + 32u * kk);
+                            mma_tf32(d, dh, dh, idesc, acc);
+                            mma_tf32(d, dh, dl, idesc, 1u);
+                            mma_tf32(d, dl, dh, idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(&empty[s]);
                 if (t % kChunkStages == kChunkStages - 1 || t == nst - 1) mma_commit(&accfull[c & 1]);
+                if (++s == a.nstage) {
+                    s = 0;
+                    ++u;
+                }
             }
             // every MMA issued so far has completed once `fin` flips
             mma_commit(fin);
@@ -366,7 +394,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         };
         bool ok = true;
         int pending = -1;                                          // finished chunk not yet drained
-        const int nf4 = a.L * 8;                                   // float4s of the data lines
+        const int nf4a = a.L * 8;                                  // float4s of the data lines of a tile
+        const int nf4 = kTcAtoms * nf4a;
         for (int t = 0; t < nst && ok; ++t) {
             const int s = t % a.nstage, u = t / a.nstage;
             // one non-blocking look per stage for a finished chunk, then sleep in try_wait until
@@ -379,13 +408,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 ok = false;
                 break;
             }
-            float4* hi = reinterpret_cast<float4*>(smem + (size_t)s * stage_bytes);
-            float4* lo = reinterpret_cast<float4*>(smem + (size_t)s * stage_bytes + lo_bytes);
             for (int f = wt; f < nf4; f += kTcWorkers) {
-                const float4 v = hi[f];
+                const int at = f / nf4a, g = f - at * nf4a;
+                unsigned char* tile = smem + (size_t)s * stage_bytes + (size_t)at * atom_bytes;
+                float4* hi = reinterpret_cast<float4*>(tile);
+                float4* lo = reinterpret_cast<float4*>(tile + lo_bytes);
+                const float4 v = hi[g];
                 const float4 h = tf32_hi(v);
-                hi[f] = h;
-                lo[f] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                lo[g] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
             }
             fence_proxy_async();
             mbar_arrive(&ready[s]);
@@ -538,13 +568,13 @@ bool launch_gram_tc(const G32Block* blk, int nblk, const G32Out* out, int nout, 
     for (int oi = 0; oi < nout; ++oi) a.out[oi] = out[oi];
     a.part_stride = part_stride;
     a.rows_per_chunk = ceil_div(ceil_div(n, nchunks), 128) * 128;
-    const int stage_bytes = a.stage_lines * 128;
+    const int stage_bytes = kTcAtoms * a.stage_lines * 128;
     a.nstage = std::max(2, std::min(8, kTcSmemBudget / stage_bytes));
     a.tx = 0;
     int k = 0;
     for (int b = 0; b < nblk; ++b) {
         if (blk[b].w <= 0) continue;
-        encode_f32_cols(&a.map[k], blk[b].p, n, blk[b].w, ld, kTcStagePts, true);
+        encode_f32_cols(&a.map[k], blk[b].p, n, blk[b].w, ld, 32, true);
         a.tx += (unsigned)(kTcStagePts * blk[b].w * sizeof(float));
         ++k;
     }

@@ -61,7 +61,7 @@ def test_mixed_matches_fp64_oracle(dims, scale, m, levels, engine):
     s.close()
 
 
-@pytest.mark.parametrize("engine", ["tensor", "simt"])
+@pytest.mark.parametrize("engine", ["auto", "tensor", "simt"])
 def test_mixed_c2_full_size(engine):
     """128^3 (2,097,152 unknowns), m = 16, 6-level V-cycle: the bench workload in mixed form."""
     dims, m = (128, 128, 128), 16
