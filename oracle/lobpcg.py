@@ -1,13 +1,15 @@
-"""Block LOBPCG with soft locking, B = I, no constraints.
+"""Block LOBPCG with soft locking, B = I, optional constraints.
 
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 Follows the algorithm of Section 2.2 ("The Detailed Description of the LOBPCG
 Algorithm", steps 1-33) with B = I (so BX = X, BW = W, BP = P and 6m vectors
-are stored, as the paper notes after the algorithm) and no constraint block Y
-(steps 2 and 10 are empty).  Soft locking as in Section 2.3: only the active
-columns J get residuals, preconditioned residuals and directions; all m
-columns of X stay in the Rayleigh-Ritz basis.
+are stored, as the paper notes after the algorithm).  Soft locking as in
+Section 2.3: only the active columns J get residuals, preconditioned residuals
+and directions; all m columns of X stay in the Rayleigh-Ritz basis.  A
+constraint block Y (l linearly independent columns; the hard locking of
+Section 2.3) enters in step 2, X = X - Y (Y^T Y)^-1 (Y^T X), and in step 10,
+W_J = W_J - Y (Y^T Y)^-1 (Y^T W_J); without Y both steps are empty.
 
 Readings of points the paper leaves open (each listed in the design notes):
 * convergence test (step 8): column j leaves J when ||A x_j - lambda_j x_j||_2
@@ -26,11 +28,15 @@ Readings of points the paper leaves open (each listed in the design notes):
   is dropped for that iteration (k = 0 form of steps 21-22 and 30-32); if
   chol(X^T X) or chol(W_J^T W_J) fails the solve stops with status "breakdown".
 * at exit every residual is recomputed from A X (not the implicitly updated AX).
+* constraints: (Y^T Y)^-1 is applied through the scale-invariant Cholesky factor
+  of Y^T Y; if that factorisation fails (Y not linearly independent) the solve
+  stops with status "breakdown" before step 3.
 """
 
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.linalg
 
 from . import laplace
 from .dense import Breakdown, scaled_cholesky, apply_inverse_upper, symmetrize, rayleigh_ritz
@@ -75,13 +81,26 @@ def upper_block_gram(S, AS):
     return G
 
 
+def constraint_projector(Y):
+    """V -> V - Y (Y^T Y)^-1 (Y^T V) (steps 2 and 10 with B = I), with Y^T Y = R^T R from the
+    scale-invariant Cholesky; raises Breakdown if Y^T Y is not positive definite."""
+    R = scaled_cholesky(Y.T @ Y)
+
+    def project(V):
+        C = Y.T @ V
+        Z = scipy.linalg.solve_triangular(R, scipy.linalg.solve_triangular(R, C, trans="T"))
+        return V - Y @ Z
+    return project
+
+
 def _converged(norm, lam, tol, tol_mode):
     bound = tol * abs(lam) if tol_mode == "relative" else tol
     return norm <= bound
 
 
-def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False, on_pass=None):
-    """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity).
+def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False, on_pass=None, Y=None):
+    """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity),
+    in the complement of the constraint block Y ((n, l) array or None).
 
     ``on_pass(k)`` (optional) is called after steps 9-33 of pass k, for timing only.
     """
@@ -91,6 +110,14 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
     if not np.all(np.isfinite(X)):
         return Result(np.full(m, np.nan), X, 0, "nonfinite", np.full(m, np.nan))
     precond = (lambda R: R) if T is None else T
+    constrain = None
+    if Y is not None and Y.shape[1] > 0:
+        try:
+            constrain = constraint_projector(np.asarray(Y, dtype=np.float64))
+        except Breakdown:
+            return Result(np.full(m, np.nan), X, 0, "breakdown", np.full(m, np.nan))
+        # Step 2: apply the constraints to X.
+        X = constrain(X)
 
     # Step 3: orthonormalise X (B = I): R = chol(X^T X), X = X R^-1, AX = A X.
     try:
@@ -129,6 +156,9 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
             break
         # Step 9: precondition.
         W = precond(W)
+        # Step 10: apply the constraints to the preconditioned residuals.
+        if constrain is not None:
+            W = constrain(W)
         # Step 11: orthonormalise W_J.
         try:
             R = scaled_cholesky(W.T @ W)
