@@ -171,6 +171,24 @@ int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timin
 #define LOBPCG_ENGINE_TENSOR   2
 int lobpcg_set_gram_engine(lobpcg_t* h, int engine);
 
+/* Constraints, the hard locking of the paper's Section 2.3 (Section 2.2, steps 2
+ * and 10): Y is an n-by-l block (column j at Y + j * ldy, float64, device memory,
+ * or host memory if on_host != 0) of l linearly independent columns; it is
+ * copied.  The following solves work in the complement of span(Y): step 2
+ * projects the initial block, X = X - Y (Y^T Y)^-1 (Y^T X), and step 10 every
+ * preconditioned residual block, W_J = W_J - Y (Y^T Y)^-1 (Y^T W_J) (B = I), so
+ * with the eigenvectors of earlier solves as Y a solve continues the spectrum
+ * (the repeated calls the paper recommends for many eigenpairs).  The library
+ * applies the same projector through an orthonormal basis of span(Y), built
+ * at the next solve in float64 (block Gram-Schmidt and Cholesky QR, twice); the
+ * mixed form projects its float32 W_J twice against a float32 copy and
+ * re-projects X in float64 before each float64 sweep.  l = 0 removes the
+ * constraints.  Returns ERR_ARG for l < 0, 2 l >= n, a NULL Y with l > 0 or
+ * ldy < n; the next solve returns ERR_ARG if 2 (m + l) > n and ERR_BREAKDOWN
+ * if Y^T Y is not numerically positive definite. */
+int lobpcg_set_constraints(lobpcg_t* h, const double* Y, int l, int64_t ldy,
+                           int on_host);
+
 /* Supply the initial block X0 (Algorithm input X): n-by-m, column-major, leading
  * dimension ldx, copied into the handle.  on_host = 1: X0 is host memory;
  * 0: device memory.  Used by the next lobpcg_solve / lobpcg_begin with the same

@@ -50,6 +50,7 @@ _SIGNATURES = {
     "lobpcg_set_options": (c_int, [c_void_p, c_int, c_int, c_int]),
     "lobpcg_set_gram_engine": (c_int, [c_void_p, c_int]),
     "lobpcg_set_initial": (c_int, [c_void_p, c_void_p, c_int, c_int64, c_int]),
+    "lobpcg_set_constraints": (c_int, [c_void_p, c_void_p, c_int, c_int64, c_int]),
     "lobpcg_solve": (c_int, [c_void_p, c_int, c_double, c_int, c_uint64, ctypes.POINTER(Info)]),
     "lobpcg_begin": (c_int, [c_void_p, c_int, c_double, c_uint64]),
     "lobpcg_iterate": (c_int, [c_void_p, c_int, ctypes.POINTER(Info)]),
@@ -126,6 +127,10 @@ def lobpcg_set_gram_engine(h, engine):
 
 def lobpcg_set_initial(h, X0, m, ldx, on_host):
     return _call("lobpcg_set_initial", h, X0, m, ldx, on_host)
+
+
+def lobpcg_set_constraints(h, Y, l, ldy, on_host):
+    return _call("lobpcg_set_constraints", h, Y, l, ldy, on_host)
 
 
 def lobpcg_solve(h, m, tol, maxit, seed, info):

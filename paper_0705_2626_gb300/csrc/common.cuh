@@ -155,6 +155,11 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
                    void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
                    cudaStream_t st, float* Xh = nullptr, float* Xl = nullptr);
 
+// Coefficients of the constraint projection V - Y (Y^T V) (steps 2 and 10 with an orthonormal
+// Y): C ((b + k) x b) = [I; -(Y^T V)] from the Gram matrix G of [V Y] ((b + k) x (b + k)), for
+// launch_update over the blocks [V Y].
+void launch_proj_coef(int b, int k, const double* G, double* C, cudaStream_t st);
+
 // gramA / gramB of the residual form from its partial sums (nparts chunks of 2 q^2 doubles,
 // q = m + b + bp; see launch_gram_mx2).
 void launch_gram_finalize_mx(int q, int m, int b, int bp, int nparts, const double* part,

@@ -591,3 +591,23 @@ void launch_gram_finalize_mx(int q, int m, int b, int bp, int nparts, const doub
     LG_CHECK_LAUNCH();
 }
 }  // namespace lg
+
+namespace lg {
+namespace {
+// C (q x b, column-major, q = b + k): rows 0..b-1 the identity, rows b..q-1 minus the cross block
+// Y^T V of the Gram matrix G of [V Y] (q x q), so that [V Y] C = V - Y (Y^T V).
+__global__ void k_proj_coef(int b, int k, const double* __restrict__ G, double* __restrict__ C) {
+    const int q = b + k;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= q * b) return;
+    const int i = e % q, j = e / q;
+    C[e] = i < b ? (i == j ? 1.0 : 0.0) : -G[j + (int64_t)q * i];
+}
+}  // namespace
+
+void launch_proj_coef(int b, int k, const double* G, double* C, cudaStream_t st) {
+    const int total = (b + k) * b;
+    k_proj_coef<<<(unsigned)ceil_div(total, 128), 128, 0, st>>>(b, k, G, C);
+    LG_CHECK_LAUNCH();
+}
+}  // namespace lg

@@ -96,6 +96,12 @@ struct lobpcg_handle {
     Buf X0;
     int X0_m = 0;
 
+    // constraint block Y (steps 2 and 10): an orthonormal basis Q of span(Y), float64, and its
+    // float32 copy for the mixed form; orthonormalised at the first solve after it is set
+    Buf Yq, Yq32;
+    int ncon = 0;
+    bool con_ready = false;
+
     // solve state
     int state = 0;      // 0 none, 1 iterating, 2 finished
     int m = 0;
@@ -506,6 +512,85 @@ unsigned fetch_small(lobpcg_t* h) {
 // Steps 3-4 on the current X, all in float64: X = X R^-1 with R = chol(X^T X), AX = A X,
 // (X^T AX) TMP = TMP Lambda, X = X TMP, AX = AX TMP; then step 7 for all m columns.
 // This is the setup of the algorithm and, in the mixed form, the float64 correction sweep.
+// ------------------------------------------------------------------ constraints (steps 2 and 10)
+// The handle keeps an orthonormal basis Q of span(Y); with it the projector
+// Y (Y^T Y)^-1 Y^T of steps 2 and 10 (B = I) is Q Q^T, applied chunk by chunk (chunks of Q sized
+// so that [V Q_c] fits the Gram scratch of the workspace: b + k <= 3 wm).
+void free_constraints(lobpcg_t* h) {
+    dfree(h, h->Yq);
+    dfree(h, h->Yq32);
+    h->ncon = 0;
+    h->con_ready = false;
+}
+
+// V <- V - Qc (Qc^T V) for one chunk Qc (k columns) of the float64 basis; V float64, b columns.
+void project_chunk64(lobpcg_t* h, int b, double* V, const double* Qc, int k) {
+    const Blocks3 S = blocks(V, b, DT_F64, Qc, k, nullptr, 0, DT_F64, h->ld);
+    gram(h, S, nullptr, h->gramA, h->gramB, nullptr);            // gramB = [V Qc]^T [V Qc]
+    launch_proj_coef(b, k, h->gramB, h->gramA, h->stream);       // gramA <- [I; -Qc^T V]
+    launch_update(h->g.n(), b, S, h->gramA, V, nullptr, h->ld, nullptr, 0u, h->stream);
+}
+
+// Steps 2 / 10: V <- V - Y (Y^T Y)^-1 Y^T V for the b columns of V (type t).  Float64: one pass
+// over the chunks of Q.  Float32 (mixed form, step 10 on W_J): two passes of block Gram-Schmidt
+// against the float32 copy of Q (the float32 roundings of one pass leave ~1e-7 of span(Y)).
+void apply_constraints(lobpcg_t* h, int b, DType t, void* V) {
+    if (h->ncon == 0 || b == 0) return;
+    const int64_t n = h->g.n();
+    const int kc = std::min(32, 2 * h->wm);
+    if (t == DT_F64) {
+        for (int c0 = 0; c0 < h->ncon; c0 += kc)
+            project_chunk64(h, b, static_cast<double*>(V), static_cast<const double*>(col(h->Yq, DT_F64, h->ld, c0)),
+                            std::min(kc, h->ncon - c0));
+        return;
+    }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c0 = 0; c0 < h->ncon; c0 += kc) {
+            const int k = std::min(kc, h->ncon - c0);
+            const float* Qc = static_cast<const float*>(col(h->Yq32, DT_F32, h->ld, c0));
+            launch_gram32_cross(n, h->ld, Qc, k, nullptr, 0, static_cast<const float*>(V), b, h->gramB, nullptr,
+                                f64(h->part), (int64_t)h->part_doubles, h->status, use_tc(h), h->stream);
+            launch_project32(n, b, static_cast<float*>(V), Qc, k, nullptr, 0, h->ld, h->gramB, k, h->status,
+                             h->stream);
+        }
+}
+
+// Orthonormalise the constraint block in place (block Gram-Schmidt against the earlier chunks and
+// Cholesky QR within a chunk, each twice), then the float32 copy.  ERR_BREAKDOWN if Y^T Y is not
+// numerically positive definite.
+void prepare_constraints(lobpcg_t* h) {
+    if (h->ncon == 0 || h->con_ready) return;
+    const int64_t n = h->g.n();
+    cudaStream_t st = h->stream;
+    const int kc = std::max(1, std::min(32, (3 * h->wm) / 2));
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+    for (int c0 = 0; c0 < h->ncon; c0 += kc) {
+        const int k = std::min(kc, h->ncon - c0);
+        double* Yk = static_cast<double*>(col(h->Yq, DT_F64, h->ld, c0));
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j0 = 0; j0 < c0; j0 += kc)
+                project_chunk64(h, k, Yk, static_cast<const double*>(col(h->Yq, DT_F64, h->ld, j0)),
+                                std::min(kc, c0 - j0));
+            const Blocks3 S = blocks(Yk, k, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
+            gram(h, S, nullptr, h->gramA, h->gramB, nullptr);
+            launch_chol_rinv(k, h->gramB, h->gramA, h->status, ST_X_BREAKDOWN, 0u, st);
+            launch_apply_rinv(n, k, DT_F64, Yk, h->ld, Yk, h->ld, h->gramA, h->status, ST_X_BREAKDOWN, st);
+        }
+    }
+    unsigned stw = 0;
+    LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    LG_CUDA(cudaStreamSynchronize(st));
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+    if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+    if (stw & (ST_X_BREAKDOWN | ST_NONFINITE))
+        throw Error(LOBPCG_ERR_BREAKDOWN, "the constraint block Y is not numerically linearly independent");
+    if (h->precision == LOBPCG_MIXED) {
+        ensure(h, h->Yq32, (size_t)h->ld * h->ncon * sizeof(float));
+        launch_convert(n, h->ncon, DT_F64, h->Yq.p, h->ld, DT_F32, h->Yq32.p, h->ld, st);
+    }
+    h->con_ready = true;
+}
+
 void orthonormalize_and_rr(lobpcg_t* h) {
     const int64_t n = h->g.n();
     const int m = h->m;
@@ -543,6 +628,8 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     const int64_t n = h->g.n();
     LG_REQUIRE(m >= 1 && m <= LOBPCG_MAX_M, LOBPCG_ERR_ARG, "m out of range [1, 32]");
     LG_REQUIRE(2 * (int64_t)m <= n, LOBPCG_ERR_ARG, "m too large for the grid (need m <= n/2)");
+    LG_REQUIRE(2 * ((int64_t)m + h->ncon) <= n, LOBPCG_ERR_ARG,
+               "m plus the constraint columns too large for the grid (need m + l <= n/2)");
     LG_REQUIRE(tol >= 0.0 && std::isfinite(tol), LOBPCG_ERR_ARG, "tol must be finite and >= 0");
     ensure_workspace(h, m);
     events_create(h);
@@ -560,6 +647,9 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     // input block
     if (h->X0.p && h->X0_m == m) copy_cols(h, m, n, DT_F64, h->X0.p, n, h->X.p, h->ld);
     else launch_random_block(seed, n, m, f64(h->X), h->ld, st);
+    // step 2: apply the constraints to X
+    prepare_constraints(h);
+    apply_constraints(h, m, DT_F64, h->X.p);
     // steps 3-5 and step 7 of k = 0
     orthonormalize_and_rr(h);
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], st));
@@ -641,6 +731,8 @@ void pass_body(lobpcg_t* h) {
     precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
     tm.mark(1);
+    // step 10: apply the constraints to the preconditioned residuals
+    apply_constraints(h, b, tw, h->W.p);
     if (mixed) project_out(h, b, h->W.p, nullptr, h->Gsmall);
     // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form has the Gram from its projection)
     if (!mixed) block_gram(h, b, tw, h->W.p, h->Gsmall);
@@ -745,6 +837,7 @@ void pass_body(lobpcg_t* h) {
 void fp64_correction(lobpcg_t* h) {
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     sync_x_from_planes(h);
+    apply_constraints(h, h->m, DT_F64, h->X.p);     // step 2 in float64 before steps 3-4
     orthonormalize_and_rr(h);
     const unsigned stw = fetch_small(h);
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
@@ -900,6 +993,7 @@ int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz, double sc
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
         free_varcoef(h);
+        free_constraints(h);
         h->X0_m = 0;
         h->g = Grid3{nx, ny, nz};
         h->scale = scale;
@@ -1027,6 +1121,25 @@ int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on
     });
 }
 
+int lobpcg_set_constraints(lobpcg_t* h, const double* Y, int l, int64_t ldy, int on_host) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(l >= 0 && 2 * (int64_t)l < n && (l == 0 || (Y && valid_ld(ldy, n))), LOBPCG_ERR_ARG,
+                   "invalid constraint block");
+        h->state = 0;      // a solve in progress used the previous constraints
+        free_constraints(h);
+        if (l == 0) return LOBPCG_OK;
+        const int64_t ld = round_up(n, 32);          // the workspace's leading dimension
+        ensure(h, h->Yq, (size_t)ld * l * sizeof(double));
+        LG_CUDA(cudaMemcpy2DAsync(h->Yq.p, ld * sizeof(double), Y, ldy * sizeof(double), n * sizeof(double), l,
+                                  on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        h->ncon = l;
+        return LOBPCG_OK;
+    });
+}
+
 int lobpcg_begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     if (h) h->launches_at_start = g_kernel_launches.load();
     return guarded(h, [&] {
@@ -1126,6 +1239,7 @@ int lobpcg_destroy(lobpcg_t* h) {
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
         free_varcoef(h);
+        free_constraints(h);
         cudaStreamSynchronize(h->stream);
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);

@@ -140,6 +140,21 @@ class Solver:
         _check(capi.lobpcg_set_initial(self.h, ctypes.c_void_p(X0.data_ptr()), X0.shape[0], X0.shape[1],
                                        on_host), self.h)
 
+    def set_constraints(self, Y):
+        """Constraint block (hard locking, steps 2 and 10): Y an (l, n) float64 tensor (host or
+        device), row j = column j; None or l = 0 removes the constraints."""
+        if Y is None:
+            _check(capi.lobpcg_set_constraints(self.h, None, 0, self.n, 0), self.h)
+            return
+        Y = torch.as_tensor(Y, dtype=torch.float64).contiguous()
+        if Y.dim() != 2 or Y.shape[1] != self.n:
+            raise ValueError(f"Y must have shape (l, {self.n})")
+        on_host = 0 if Y.is_cuda else 1
+        if Y.is_cuda:
+            torch.cuda.current_stream(self.device).synchronize()
+        _check(capi.lobpcg_set_constraints(self.h, ctypes.c_void_p(Y.data_ptr()) if Y.shape[0] else None,
+                                           Y.shape[0], self.n, on_host), self.h)
+
     def solve(self, m, tol=1e-8, maxit=200, seed=2, with_vectors=True):
         rc = capi.lobpcg_solve(self.h, m, tol, maxit, seed, ctypes.byref(self.info))
         self.m = m
