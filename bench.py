@@ -332,6 +332,32 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_inner_pcg_sweep(args):
+    """Section 4.2's experiment on this workload: float64 time to tol 1e-8 and outer iterations
+    against the number of inner PCG iterations (0 = the V-cycle applied directly); one JSON line."""
+    import torch
+    from paper_0705_2626_gb300.solver import Solver
+
+    d = WORKLOADS[args.workload]
+    dims, m, levels = d["dims"], d["m"], d["levels"]
+    torch.cuda.set_device(0)
+    s = Solver(dims, levels=levels)
+    s.solve(m, tol=1e-8, maxit=300, seed=2, with_vectors=False)        # warm-up
+    rows = []
+    for k in [int(x) for x in args.inner_pcg_sweep.split(",")]:
+        s.set_inner_pcg(k)
+        best = None
+        for rep in range(3):
+            out = s.solve(m, tol=1e-8, maxit=300, seed=2, with_vectors=False)
+            t = out["solve_ms"] / 1e3
+            best = t if best is None else min(best, t)
+        rows.append(dict(inner_iters=k, time_to_tol_s=best, outer_iters=out["iters"], status=out["status_name"],
+                         max_rel_resid=out["max_rel_resid"]))
+    s.close()
+    print(json.dumps(dict(metric="time to tol 1e-8 vs inner PCG iterations (float64)", config=workload_desc(args.workload),
+                          rows=rows)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,7 +366,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner-pcg-sweep", default=None,
+                    help="comma-separated inner PCG iteration counts: print that sweep instead of the bench line")
     args = ap.parse_args()
+    if args.inner_pcg_sweep:
+        run_inner_pcg_sweep(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -149,6 +149,17 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre,
  * per-phase device timing (0/1; adds event records inside each iteration). */
 int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timing);
 
+/* Inner PCG preconditioning (the paper's Section 4.2, "Performance Versus the
+ * Number of Inner Iterations"): step 9 applies T = k iterations of
+ * preconditioned conjugate gradients for A E = W_J from E = 0, preconditioned by
+ * the preconditioner set with lobpcg_set_preconditioner, each column an
+ * independent solve (float64; a column stops early only if p^T A p <= 0 or
+ * r^T z <= 0).  iters = 0 (default) applies the preconditioner directly.  T is
+ * then a nonlinear map, which LOBPCG tolerates.  lobpcg_op_precond applies the
+ * same T.  Returns ERR_ARG for iters < 0 or > 10000, or iters > 0 on a
+ * LOBPCG_MIXED handle. */
+int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
+
 /* Engine of the float32 Gram products of the mixed form (steps 11, 15, 17-23;
  * the double-float X^T X block is unaffected):
  *   LOBPCG_ENGINE_TENSOR: tcgen05 tensor-core MMAs on 3 x TF32 splits (hi*hi +

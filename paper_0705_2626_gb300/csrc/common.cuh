@@ -232,6 +232,21 @@ void launch_dense_apply(int n, int ncols, const double* Ainv, const double* r, i
 // grad[f] = scale sum_i w[i] (x_i,q - x_i,p)^2 (w host array of m weights).
 void launch_vc_grad(const Grid3& g, int m, const double* w, double scale, const double* X, int64_t ldx,
                     double* grad, cudaStream_t st);
+// ---------------------------------------------------------------- inner PCG (k_pcg.cu)
+// b independent PCG solves, float64 columns with leading dimension ld.  Column dots u_j . v_j into
+// out[j] via pcg_chunks(n) * b partial sums (fixed-order chunk sums); act[j] is cleared when
+// out[j] <= 0 (act may not be null).
+int pcg_chunks(int64_t n);
+void launch_coldot(int64_t n, int b, const double* U, const double* V, int64_t ld, double* partial, double* out,
+                   int* act, cudaStream_t st);
+void launch_fill_int(int b, int v, int* a, cudaStream_t st);
+// E += alpha P, R -= alpha AP, alpha_j = rz_j / pap_j, on columns with act[j].
+void launch_pcg_er(int64_t n, int b, const double* rz, const double* pap, const int* act, double* E, double* R,
+                   const double* P, const double* AP, int64_t ld, cudaStream_t st);
+// P = Z + beta P, beta_j = rz_new_j / rz_j, on columns with act[j].
+void launch_pcg_p(int64_t n, int b, const double* rz_new, const double* rz, const int* act, double* P,
+                  const double* Z, int64_t ld, cudaStream_t st);
+
 // ---------------------------------------------------------------- small dense
 // Rinv = R^-1, R = chol(G) on the unit-diagonal scaling of G (b x b).  On failure sets
 // fail_bit in *status and leaves Rinv unspecified.  Skipped if *status & skip_mask.

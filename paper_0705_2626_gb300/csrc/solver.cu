@@ -76,6 +76,8 @@ struct lobpcg_handle {
     // options
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
     int gram_engine = LOBPCG_ENGINE_AUTO;       // float32 Grams of the mixed form
+    int inner_pcg = 0;                          // inner PCG iterations of step 9 (0: V-cycle directly)
+    Buf pcg_small;                              // inner PCG scalars: rz, rz', pAp (b each), active flags
 
     // workspace for a block of wm columns
     int wm = 0;
@@ -364,6 +366,36 @@ void precond(lobpcg_t* h, int b, DType t, const void* r, int64_t ldr, void* e, i
         return;
     }
     vcycle(h, 0, b, t, r, ldr, e, lde, tmp, ldt);
+}
+
+// Step 9 with an inner PCG solve (Section 4.2): E = T_k(R) = the k-th iterate (k = inner_pcg) of
+// PCG for A E = R from E = 0, preconditioned by the V-cycle, columns independent; float64, all
+// blocks with the workspace's leading dimension.  R is overwritten (it becomes the PCG residual);
+// Z, P, AP and tmp are scratch blocks of b columns.
+void inner_pcg(lobpcg_t* h, int b, double* R, double* E, double* Z, double* P, double* AP, double* tmp) {
+    const int64_t n = h->g.n(), ld = h->ld;
+    cudaStream_t st = h->stream;
+    ensure(h, h->pcg_small, (size_t)LOBPCG_MAX_M * (3 * sizeof(double) + sizeof(int)));
+    double* rz = f64(h->pcg_small);
+    double* rz_new = rz + LOBPCG_MAX_M;
+    double* pap = rz_new + LOBPCG_MAX_M;
+    int* act = reinterpret_cast<int*>(pap + LOBPCG_MAX_M);
+    double* part = f64(h->part);
+    LG_REQUIRE((size_t)pcg_chunks(n) * b <= h->part_doubles, LOBPCG_ERR_ARG, "PCG scratch too small");
+    LG_CUDA(cudaMemsetAsync(E, 0, (size_t)ld * b * sizeof(double), st));
+    precond(h, b, DT_F64, R, ld, Z, ld, tmp, ld);                    // z_0 = M r_0
+    copy_cols(h, b, n, DT_F64, Z, ld, P, ld);                        // p_0 = z_0
+    launch_fill_int(b, 1, act, st);
+    launch_coldot(n, b, R, Z, ld, part, rz, act, st);
+    for (int it = 0; it < h->inner_pcg; ++it) {
+        spmv(h, b, DT_F64, P, ld, AP, ld);
+        launch_coldot(n, b, P, AP, ld, part, pap, act, st);
+        launch_pcg_er(n, b, rz, pap, act, E, R, P, AP, ld, st);
+        precond(h, b, DT_F64, R, ld, Z, ld, tmp, ld);
+        launch_coldot(n, b, R, Z, ld, part, rz_new, act, st);
+        launch_pcg_p(n, b, rz_new, rz, act, P, Z, ld, st);
+        std::swap(rz, rz_new);
+    }
 }
 
 // ------------------------------------------------------------------ Gram helpers
@@ -728,7 +760,10 @@ void pass_body(lobpcg_t* h) {
                                         cudaMemcpyDeviceToDevice, st));
         }
     }
-    precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
+    if (h->inner_pcg > 0 && !mixed)
+        inner_pcg(h, b, f64(h->W), f64(h->E0), f64(h->Pc), f64(h->APc), f64(h->AW), f64(h->T0));
+    else
+        precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
     tm.mark(1);
     // step 10: apply the constraints to the preconditioned residuals
@@ -992,6 +1027,7 @@ int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz, double sc
         free_workspace(h);
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
+        dfree(h, h->pcg_small);
         free_varcoef(h);
         free_constraints(h);
         h->X0_m = 0;
@@ -1090,6 +1126,16 @@ int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timin
         h->tol_mode = tol_mode;
         h->gram_mode = gram_mode;
         h->phase_timing = phase_timing ? 1 : 0;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_set_inner_pcg(lobpcg_t* h, int iters) {
+    return guarded(h, [&] {
+        LG_REQUIRE(iters >= 0 && iters <= 10000, LOBPCG_ERR_ARG, "inner PCG iterations out of range [0, 10000]");
+        LG_REQUIRE(iters == 0 || h->precision == LOBPCG_FP64, LOBPCG_ERR_ARG,
+                   "inner PCG needs a LOBPCG_FP64 handle");
+        h->inner_pcg = iters;
         return LOBPCG_OK;
     });
 }
@@ -1238,6 +1284,7 @@ int lobpcg_destroy(lobpcg_t* h) {
         free_workspace(h);
         dfree(h, h->coarse_tab);
         dfree(h, h->X0);
+        dfree(h, h->pcg_small);
         free_varcoef(h);
         free_constraints(h);
         cudaStreamSynchronize(h->stream);
@@ -1282,7 +1329,13 @@ int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr, doub
         LG_REQUIRE(h->precision == LOBPCG_FP64, LOBPCG_ERR_ARG,
                    "lobpcg_op_precond needs a LOBPCG_FP64 handle");
         ensure_workspace(h, std::max(h->wm, ncols));
-        precond(h, ncols, DT_F64, R, ldr, E, lde, h->T0.p, h->ld);
+        if (h->inner_pcg > 0) {
+            copy_cols(h, ncols, n, DT_F64, R, ldr, h->W.p, h->ld);
+            inner_pcg(h, ncols, f64(h->W), f64(h->E0), f64(h->Pc), f64(h->APc), f64(h->AW), f64(h->T0));
+            copy_cols(h, ncols, n, DT_F64, h->E0.p, h->ld, E, lde);
+        } else {
+            precond(h, ncols, DT_F64, R, ldr, E, lde, h->T0.p, h->ld);
+        }
         LG_CUDA(cudaStreamSynchronize(h->stream));
         return LOBPCG_OK;
     });

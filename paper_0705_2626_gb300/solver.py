@@ -140,6 +140,10 @@ class Solver:
         _check(capi.lobpcg_set_initial(self.h, ctypes.c_void_p(X0.data_ptr()), X0.shape[0], X0.shape[1],
                                        on_host), self.h)
 
+    def set_inner_pcg(self, iters):
+        """Step 9 as `iters` inner PCG iterations preconditioned by the V-cycle (0: V-cycle directly)."""
+        _check(capi.lobpcg_set_inner_pcg(self.h, int(iters)), self.h)
+
     def set_constraints(self, Y):
         """Constraint block (hard locking, steps 2 and 10): Y an (l, n) float64 tensor (host or
         device), row j = column j; None or l = 0 removes the constraints."""
