@@ -358,6 +358,37 @@ def run_inner_pcg_sweep(args):
                           rows=rows)))
 
 
+def run_block_size_sweep(args):
+    """Section 4.3's experiment on this grid: seconds per iteration (every column active) and time
+    to tol 1e-8 against the block size m, both forms; one JSON line."""
+    import torch
+    from paper_0705_2626_gb300.solver import Solver
+
+    d = WORKLOADS[args.workload]
+    dims, levels = d["dims"], d["levels"]
+    torch.cuda.set_device(0)
+    rows = []
+    for m in [int(x) for x in args.m_sweep.split(",")]:
+        for precision in ("fp64", "mixed"):
+            s = Solver(dims, levels=levels, precision=precision)
+            s.begin(m, tol=0.0, seed=2)
+            s.iterate(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.iterate(10)
+            e1.record(s.stream)
+            e1.synchronize()
+            ms_it = e0.elapsed_time(e1) / 10
+            out = s.solve(m, tol=1e-8, maxit=300, seed=2, with_vectors=False)
+            rows.append(dict(m=m, precision=precision, ms_per_iter=ms_it, ms_per_iter_per_col=ms_it / m,
+                             time_to_tol_s=out["solve_ms"] / 1e3, iters=out["iters"], status=out["status_name"]))
+            s.close()
+            torch.cuda.empty_cache()
+    print(json.dumps(dict(metric="ms per iteration and time to tol 1e-8 vs block size m",
+                          config=workload_desc(args.workload), rows=rows)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,7 +399,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner-pcg-sweep", default=None,
                     help="comma-separated inner PCG iteration counts: print that sweep instead of the bench line")
+    ap.add_argument("--m-sweep", default=None,
+                    help="comma-separated block sizes: print that sweep instead of the bench line")
     args = ap.parse_args()
+    if args.m_sweep:
+        run_block_size_sweep(args)
+        return
     if args.inner_pcg_sweep:
         run_inner_pcg_sweep(args)
         return
