@@ -271,6 +271,14 @@ int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx,
 int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,
                       double* E, int64_t lde);
 
+/* The mixed form's preconditioner (Algorithm step 9 on a LOBPCG_MIXED handle):
+ * E = T R for ncols float32 device columns (n rows, leading dimensions ldr, lde
+ * >= n), the V-cycle with float32 arithmetic on every level, float32 storage on
+ * the finest and bfloat16 storage on the coarser levels.  ERR_ARG on a
+ * LOBPCG_FP64 handle. */
+int lobpcg_op_precond_f32(lobpcg_t* h, int ncols, const float* R, int64_t ldr,
+                          float* E, int64_t lde);
+
 /* Column residuals (Algorithm step 7): for t < ncols, j = cols[t] (host array),
  * W[:, t] = AX[:, j] - lambda[j] X[:, j] (lambda: device, m values) and
  * norms[t] = ||W[:, t]||_2 (host output).  W may be NULL (norms only). */

@@ -1341,6 +1341,20 @@ int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr, doub
     });
 }
 
+int lobpcg_op_precond_f32(lobpcg_t* h, int ncols, const float* R, int64_t ldr, float* E, int64_t lde) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(R && E && ncols >= 1 && ncols <= LOBPCG_MAX_M && valid_ld(ldr, n) && valid_ld(lde, n),
+                   LOBPCG_ERR_ARG, "invalid preconditioner arguments");
+        LG_REQUIRE(h->precision == LOBPCG_MIXED, LOBPCG_ERR_ARG, "lobpcg_op_precond_f32 needs a LOBPCG_MIXED handle");
+        ensure_workspace(h, std::max(h->wm, ncols));
+        precond(h, ncols, DT_F32, R, ldr, E, lde, h->T0.p, h->ld);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
 int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X, const double* AX,
                        int64_t ld, const double* lambda, double* W, int64_t ldw, double* norms) {
     return guarded(h, [&] {

@@ -68,6 +68,36 @@ def test_vcycle_matches_oracle(dims, levels, m):
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("dims,levels,m", [((9, 7, 6), 2, 2), ((15, 17, 13), 3, 3), ((40, 36, 34), 3, 4),
+                                           ((128, 128, 128), 6, 16)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_mixed_vcycle_matches_oracle(dims, levels, m):
+    """The mixed form's V-cycle (float32 level 0, bfloat16 coarse levels) against the float64
+    oracle V-cycle: the bfloat16 storage of the coarse
+    corrections (8 significant bits) bounds the difference, about 2^-9 of the coarse part; an
+    indexing error in any level would show as O(1)."""
+    scale = laplace.default_scale(dims)
+    s = Solver(dims, scale=scale, levels=levels, precision="mixed")
+    n = s.n
+    g = np.random.default_rng(2)
+    for kind in ("random", "smooth"):
+        if kind == "random":
+            R = g.standard_normal((n, m))
+        else:   # smooth right-hand sides: the coarse correction carries most of T R
+            R = np.stack([laplace.exact_eigenvector(dims, (1 + j % 2, 1 + j % 3, 1)) for j in range(m)], axis=1)
+            R += 0.01 * g.standard_normal((n, m))
+        R32 = R.astype(np.float32)
+        Rd = torch.tensor(np.ascontiguousarray(R32.T), device="cuda")
+        Ed = torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda")
+        assert capi.lobpcg_op_precond_f32(s.h, m, ptr(Rd), n, ptr(Ed), n) == capi.OK
+        got = Ed.cpu().numpy().T.astype(np.float64)
+        want = multigrid.VCycle(dims, scale, levels)(R32.astype(np.float64))
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= 1e-2, (kind, rel)
+        assert np.max(np.abs(got - want)) <= 3e-2 * np.max(np.abs(want)), kind
+    s.close()
+
+
 def test_identity_preconditioner_copies():
     s = make((6, 5, 4), precond="none")
     R = np.random.default_rng(3).standard_normal((s.n, 3))
