@@ -203,6 +203,15 @@ void launch_planes_to_f64(int64_t n, int m, const float* Xh, const float* Xl, in
 // V <- V - [L0 L1] C for b columns of V (C (w0 + w1) x b, column-major, ld ldc, float64).
 void launch_project32(int64_t n, int b, float* V, const float* L0, int w0, const float* L1, int w1,
                       int64_t ld, const double* C, int ldc, unsigned* err, cudaStream_t st);
+// V <- [L0 L1 V] K (K (w0 + w1 + b) x b, column-major, ld ldk, float64), in place; skipped if
+// *status & skip.  With K = [-C Rinv; Rinv] it is the last Gram-Schmidt pass and the Cholesky
+// step in one pass over V.
+void launch_combine32(int64_t n, int b, float* V, const float* L0, int w0, const float* L1, int w1, int64_t ld,
+                      const double* K, int ldk, const unsigned* status, unsigned skip, unsigned* err,
+                      cudaStream_t st);
+// K = [-C Rinv; Rinv] ((w + b) x b, ld w + b) for C (w x b, ld ldc) and upper Rinv (b x b).
+void launch_projapply_coef(int w, int b, const double* C, int ldc, const double* Rinv, double* K,
+                           const unsigned* status, unsigned skip, cudaStream_t st);
 // V <- V Rinv (Rinv b x b upper triangular, ld b, float64), in place; skipped if *status & skip.
 void launch_apply32(int64_t n, int b, float* V, int64_t ld, const double* Rinv,
                     const unsigned* status, unsigned skip, unsigned* err, cudaStream_t st);

@@ -268,6 +268,25 @@ __global__ void k_sub_ctc(int w, int b, const double* __restrict__ C, int ldc, d
     G[i + (int64_t)b * j] -= s;
 }
 
+// K ((w + b) x b, column-major, ld w + b) = [-C Rinv; Rinv] for C (w x b, ld ldc) and the upper
+// triangular Rinv (b x b, ld b): [L V] K = (V - L C) Rinv.  One thread per entry; skipped if
+// *status & skip.
+__global__ void k_projapply_coef(int w, int b, const double* __restrict__ C, int ldc, const double* __restrict__ Rinv,
+                                 double* __restrict__ K, const unsigned* status, unsigned skip) {
+    if (*status & skip) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = w + b;
+    if (e >= q * b) return;
+    const int i = e % q, c = e / q;
+    double v = 0.0;
+    if (i < w) {
+        for (int k = 0; k <= c; ++k) v = fma(-C[i + (int64_t)ldc * k], Rinv[k + (int64_t)b * c], v);
+    } else if (i - w <= c) {
+        v = Rinv[(i - w) + (int64_t)b * c];
+    }
+    K[e] = v;
+}
+
 // ---------------------------------------------------------------- host side
 // Tiles of TI x TJ staged columns covering every needed entry of the outputs.
 void build_tiles(G32Args& a, int TI, int TJ) {
@@ -381,6 +400,14 @@ void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t
 void launch_gram_sub_ctc(int w, int b, const double* C, int ldc, double* G, cudaStream_t st) {
     if (b <= 0 || w <= 0) return;
     k_sub_ctc<<<(unsigned)ceil_div((int64_t)b * b, 256), 256, 0, st>>>(w, b, C, ldc, G);
+    LG_CHECK_LAUNCH();
+}
+
+void launch_projapply_coef(int w, int b, const double* C, int ldc, const double* Rinv, double* K,
+                           const unsigned* status, unsigned skip, cudaStream_t st) {
+    if (b <= 0) return;
+    k_projapply_coef<<<(unsigned)ceil_div((int64_t)(w + b) * b, 128), 128, 0, st>>>(w, b, C, ldc, Rinv, K, status,
+                                                                                   skip);
     LG_CHECK_LAUNCH();
 }
 

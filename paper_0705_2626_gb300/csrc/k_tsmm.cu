@@ -7,9 +7,11 @@
 // completion); every thread owns 4 consecutive points of a tile (float4 reads of the staged
 // columns) and kCG output columns, and writes its outputs straight to global memory with
 // float4 stores.  Because every input of a tile is in shared memory before any output of that
-// tile is written, the products can run in place.  Three forms:
+// tile is written, the products can run in place.  Four forms:
 //   PROJECT   V <- V - [L0 L1] C          (block Gram-Schmidt of the mixed form)
 //   APPLY     V <- V Rinv, Rinv upper      (Cholesky orthonormalisation, steps 11 / 15)
+//   GENERAL   V <- [L0 L1 V] K             (the last Gram-Schmidt pass and the Cholesky step in
+//                                           one pass: K = [-C Rinv; Rinv])
 //   UPDATE    P <- W C_W + P C_P (float32), X <- X C_X + P in double-float, X as hi / lo planes
 //             (Ritz update, steps 25-33)
 #include <algorithm>
@@ -26,7 +28,7 @@ constexpr int kMaxThreads = 512;
 constexpr int kHeader = 128;
 constexpr int kSmemBudget = 200 * 1024;
 
-enum TsmmMode : int { TS_PROJECT = 0, TS_APPLY = 1, TS_UPDATE = 2 };
+enum TsmmMode : int { TS_PROJECT = 0, TS_APPLY = 1, TS_UPDATE = 2, TS_GENERAL = 3 };
 
 struct TsmmArgs {
     CUtensorMap map[4];
@@ -90,7 +92,8 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int nthr = blockDim.x;
     // coefficients: [row i][col c] with row length cp; UPDATE: C_X hi, C_X lo, C_W, C_P
     const int cp = a.cp;
-    const int crows = a.mode == TS_UPDATE ? 2 * a.wl + a.b + a.bp : (a.mode == TS_PROJECT ? a.wl : a.ncols);
+    const int crows = a.mode == TS_UPDATE ? 2 * a.wl + a.b + a.bp
+                                          : (a.mode == TS_PROJECT ? a.wl : (a.mode == TS_GENERAL ? a.Q : a.ncols));
     for (int e = tid; e < crows * cp; e += nthr) {
         const int i = e / cp, c = e - i * cp;
         float v = 0.f;
@@ -212,8 +215,9 @@ __global__ void __launch_bounds__(kMaxThreads)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) acc[u][v] = f4(x, u);
                 }
-                // PROJECT: the [L0 L1] columns are staged first; APPLY: V itself (rows i <= c)
-                const int nin = a.mode == TS_PROJECT ? a.wl : min(a.ncols, c0 + kCG);
+                // PROJECT: the [L0 L1] columns are staged first; APPLY: V itself (rows i <= c);
+                // GENERAL: every staged column
+                const int nin = a.mode == TS_PROJECT ? a.wl : (a.mode == TS_GENERAL ? a.Q : min(a.ncols, c0 + kCG));
                 const float sg = a.mode == TS_PROJECT ? -1.f : 1.f;
                 for (int i = 0; i < nin; ++i) {
                     const float4 s = *reinterpret_cast<const float4*>(sm + (int64_t)i * a.TP);
@@ -267,7 +271,8 @@ void tsmm_launch(TsmmArgs& a, const TsBlock* blk, int nblk, const double* C, int
     a.TP = 256;
     while (a.TP > 64 && 3 * (int64_t)a.Q * a.TP * 4 > kSmemBudget) a.TP /= 2;
     const int64_t stage_bytes = (int64_t)a.Q * a.TP * 4;
-    const int crows = a.mode == TS_UPDATE ? 2 * a.wl + a.b + a.bp : (a.mode == TS_PROJECT ? a.wl : a.ncols);
+    const int crows = a.mode == TS_UPDATE ? 2 * a.wl + a.b + a.bp
+                                          : (a.mode == TS_PROJECT ? a.wl : (a.mode == TS_GENERAL ? a.Q : a.ncols));
     a.cp = (a.ncols + 3) & ~3;
     const int64_t coef_bytes = (int64_t)crows * a.cp * 4;
     a.nstage = (int)std::max<int64_t>(2, std::min<int64_t>(4, (kSmemBudget - coef_bytes) / stage_bytes));
@@ -315,6 +320,22 @@ void launch_project32(int64_t n, int b, float* V, const float* L0, int w0, const
     a.out0 = V;
     const TsBlock blk[3] = {{L0, w0}, {L1, w1}, {V, b}};
     tsmm_launch(a, blk, 3, C, ldc, nullptr, 0u, err, st);
+}
+
+void launch_combine32(int64_t n, int b, float* V, const float* L0, int w0, const float* L1, int w1, int64_t ld,
+                      const double* K, int ldk, const unsigned* status, unsigned skip, unsigned* err,
+                      cudaStream_t st) {
+    if (b <= 0) return;
+    static thread_local TsmmArgs a;
+    a = TsmmArgs{};
+    a.mode = TS_GENERAL;
+    a.ncols = b;
+    a.wl = w0 + w1;
+    a.ld = ld;
+    a.n = n;
+    a.out0 = V;
+    const TsBlock blk[3] = {{L0, w0}, {L1, w1}, {V, b}};
+    tsmm_launch(a, blk, 3, K, ldk, status, skip, err, st);
 }
 
 void launch_apply32(int64_t n, int b, float* V, int64_t ld, const double* Rinv, const unsigned* status,

@@ -427,29 +427,36 @@ int use_tc(const lobpcg_t* h) {
 }
 
 // Mixed form: two passes of block Gram-Schmidt of V (b float32 columns) against X (m float64
-// columns) and, if W != null, against W (b float32 columns).  The trial subspace of the
-// Rayleigh-Ritz step is unchanged; the basis [X W P] becomes well conditioned, which the
-// float32 search directions need (with near-dependent columns the float32 roundings of the Gram
-// matrices would be magnified into spurious Ritz pairs).
-// The second pass also returns G = V^T V of the projected block for its Cholesky step (11 / 15):
-// the pass computes C = [X W]^T V and V^T V before it subtracts [X W] C, and
-// (V - L C)^T (V - L C) = V^T V - C^T C when L = [X W] has orthonormal columns (to float32
-// accuracy; C is at the float32 rounding level in that pass, so the neglected term is ~1e-14).
-void project_out(lobpcg_t* h, int b, void* V, const void* W, double* G) {
+// columns, its hi plane) and, if W != null, against W (b float32 columns), then the Cholesky
+// step of 11 / 15.  The trial subspace of the Rayleigh-Ritz step is unchanged; the basis
+// [X W P] becomes well conditioned, which the float32 search directions need (with
+// near-dependent columns the float32 roundings of the Gram matrices would be magnified into
+// spurious Ritz pairs).
+// The second pass computes C2 = [X W]^T V and V^T V of its input; then G = V^T V - C2^T C2 is the
+// Gram matrix of V - L C2 (L = [X W] has orthonormal columns to float32 accuracy, and C2 is at
+// the float32 rounding level, so the neglected term is ~1e-14), R = chol(G), and one pass writes
+// V <- (V - L C2) R^-1 = [L V] [-C2 R^-1; R^-1].  fail_bit: the status bit of a failed Cholesky;
+// skip_bits: earlier failures that skip this step.
+void project_normalize(lobpcg_t* h, int b, void* V, const void* W, unsigned fail_bit, unsigned skip_bits) {
     const int64_t n = h->g.n();
     const int m = h->m;
     const int wb = W ? b : 0;
     const float* Xh = static_cast<const float*>(h->Xh.p);
     const float* Wf = static_cast<const float*>(W);
-    for (int pass = 0; pass < 2; ++pass) {
-        // coefficients [X W]^T V ((m + wb) x b) in gramB, which is free until steps 17-23
-        launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, static_cast<const float*>(V), b, h->gramB,
-                            pass == 1 ? G : nullptr, f64(h->part), (int64_t)h->part_doubles, h->status, use_tc(h),
-                            h->stream);
-        launch_project32(n, b, static_cast<float*>(V), Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status,
-                         h->stream);
-    }
-    launch_gram_sub_ctc(m + wb, b, h->gramB, m + wb, G, h->stream);
+    float* Vf = static_cast<float*>(V);
+    cudaStream_t st = h->stream;
+    // pass 1: V <- V - L (L^T V); the coefficients in gramB, which is free until steps 17-23
+    launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, Vf, b, h->gramB, nullptr, f64(h->part), (int64_t)h->part_doubles,
+                        h->status, use_tc(h), st);
+    launch_project32(n, b, Vf, Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status, st);
+    // pass 2: C2 and G, the Cholesky factor, then projection and R^-1 in one pass
+    launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, Vf, b, h->gramB, h->Gsmall, f64(h->part), (int64_t)h->part_doubles,
+                        h->status, use_tc(h), st);
+    launch_gram_sub_ctc(m + wb, b, h->gramB, m + wb, h->Gsmall, st);
+    launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, fail_bit, skip_bits, st);
+    const unsigned skip = fail_bit | skip_bits;
+    launch_projapply_coef(m + wb, b, h->gramB, m + wb, h->Rinv, h->gramA, h->status, skip, st);
+    launch_combine32(n, b, Vf, Xh, m, Wf, wb, h->ld, h->gramA, m + wb + b, h->status, skip, h->status, st);
 }
 
 // V <- V Rinv (steps 11 and 15), in place; skipped on the device if *status & skip.
@@ -768,11 +775,14 @@ void pass_body(lobpcg_t* h) {
     tm.mark(1);
     // step 10: apply the constraints to the preconditioned residuals
     apply_constraints(h, b, tw, h->W.p);
-    if (mixed) project_out(h, b, h->W.p, nullptr, h->Gsmall);
-    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form has the Gram from its projection)
-    if (!mixed) block_gram(h, b, tw, h->W.p, h->Gsmall);
-    launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
-    apply_rinv(h, b, tw, h->W.p, ST_W_BREAKDOWN);
+    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form first projects W_J against X)
+    if (mixed) {
+        project_normalize(h, b, h->W.p, nullptr, ST_W_BREAKDOWN, 0u);
+    } else {
+        block_gram(h, b, tw, h->W.p, h->Gsmall);
+        launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
+        apply_rinv(h, b, tw, h->W.p, ST_W_BREAKDOWN);
+    }
     tm.mark(2);
     // step 12: AW_J = A W_J
     spmv(h, b, tw, h->W.p, ld, h->AW.p, ld);
@@ -794,10 +804,13 @@ void pass_body(lobpcg_t* h) {
             Pj = h->Pc.p;
             APj = h->APc.p;
         }
-        if (mixed) project_out(h, b, Pj, h->W.p, h->Gsmall);
-        else block_gram(h, b, tw, Pj, h->Gsmall);
-        launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
-        apply_rinv(h, b, tw, Pj, ST_W_BREAKDOWN | ST_P_DROPPED);
+        if (mixed) {
+            project_normalize(h, b, Pj, h->W.p, ST_P_DROPPED, ST_W_BREAKDOWN);
+        } else {
+            block_gram(h, b, tw, Pj, h->Gsmall);
+            launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_P_DROPPED, ST_W_BREAKDOWN, st);
+            apply_rinv(h, b, tw, Pj, ST_W_BREAKDOWN | ST_P_DROPPED);
+        }
         if (h->precision == LOBPCG_MIXED) {
             // Mixed form: AP_J = A P_J by one more (float32) SpMV.  P_J is nearly rank deficient
             // near convergence, and R^-1 would magnify the separate float32 roundings of P_J and
