@@ -26,7 +26,7 @@ namespace {
 constexpr int kCG = 4;                  // output columns per thread
 constexpr int kMaxThreads = 512;
 constexpr int kHeader = 128;
-constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemBudget = 100 * 1024;  // two blocks per SM (one 8-warp block per SM left it latency-bound)
 
 enum TsmmMode : int { TS_PROJECT = 0, TS_APPLY = 1, TS_UPDATE = 2, TS_GENERAL = 3 };
 
