@@ -180,6 +180,22 @@ def cpu_baseline_sample(w, iters=1):
     return 1.0 / per, per
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks of the default process group (x itself when world = 1)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps, world, t_ms):
+    """Iterations per second of the whole job: each of the `world` ranks (an independent replica)
+    ran `steps` iterations, and the job took the slowest rank's time t_ms."""
+    return world * steps / (t_ms / 1e3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -220,11 +236,8 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        t = torch.tensor([x], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, world, dev)
 
     def timed_form(precision, sampler=None):
         """K iterations with every column active (tol = 0), inputs resident in HBM; then the same
@@ -245,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         clocks = sampler.stop() if sampler else None
         launches = int(s.info.kernel_launches)
-        t_ms = max_over_ranks(e0.elapsed_time(e1))
+        t_ms = rank_max(e0.elapsed_time(e1))
         s.set_options(phase_timing=True)
         s.begin(m, tol=0.0, seed=seed)
         s.iterate(args.warmup)
@@ -265,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- float64 form: the timed steps of the JSON line
     sampler = ClockSampler(local_rank)
     s64, t64, launches, ph64, clocks = timed_form("fp64", sampler)
-    value = world * args.steps / (t64 / 1e3)
+    value = replica_throughput(args.steps, world, t64)
     gram_ms = ph64["gram"]
     achieved = gram_flops_per_launch(n, m) / (gram_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get((w, kernel_source_hash()))
@@ -283,8 +296,8 @@ def run_ours(args, rank, world, local_rank):
     s64.solve(m, tol=0.0, maxit=args.steps, seed=seed)
     lam = (ctypes.c_double * m)()
     capi.lobpcg_get_eigenpairs(s64.h, lam, ctypes.c_void_p(Xout.data_ptr()), n, 1, None)
-    t_e2e = max_over_ranks(time.perf_counter() - t0)
-    e2e = dict(value=world * args.steps / t_e2e, unit="iters/s",
+    t_e2e = rank_max(time.perf_counter() - t0)
+    e2e = dict(value=replica_throughput(args.steps, world, t_e2e * 1e3), unit="iters/s",
                h2d_bytes_per_step=n * m * 8 / args.steps, d2h_bytes_per_step=(n * m * 8 + m * 8) / args.steps,
                note="set_initial(pinned host X0) + solve(tol=0, maxit=K) + get_eigenpairs(to pinned host), wall clock")
     s64.close()
@@ -326,7 +339,7 @@ def run_ours(args, rank, world, local_rank):
                     parallelism="replicas" if world > 1 else "single-gpu"),
         time_to_tol=dict(fp64=ttt64, mixed=tttmx, mixed_speedup=ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"],
                          max_rel_lambda_diff_mixed_vs_fp64=lam_diff),
-        mixed=dict(value=world * args.steps / (tmx / 1e3), unit="iters/s", ms_per_step=tmx / args.steps,
+        mixed=dict(value=replica_throughput(args.steps, world, tmx), unit="iters/s", ms_per_step=tmx / args.steps,
                    dtype="f64+f32+bf16", gpu_launches=launches_mx, phase_ms_per_iter=phmx, kernels_hbm=kernmx),
         phase_ms_per_iter=ph64, kernels_hbm=kern64,
         roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles, float64)", bound="alu",
