@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kTX* kTY)
     k_stencil_v4(Grid3 g, int zchunk, int nzc, float a, float b, const T* __restrict__ x, int64_t ldx,
                  float c, const T* __restrict__ z, int64_t ldz, T* __restrict__ y, int64_t ldy) {
     const int nx4 = g.nx >> 2;
-    const int i4 = blockIdx.x * kTX + threadIdx.x;
-    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int i4 = blockIdx.x * blockDim.x + threadIdx.x;   // block (32, 4), or (16, 8) / (8, 16) for short rows
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int col = blockIdx.z / nzc;
     const int kc = blockIdx.z - col * nzc;
     if (i4 >= nx4 || j >= g.ny) return;
@@ -188,6 +188,61 @@ __global__ void __launch_bounds__(kTX* kTY)
         }
     }
     st_as(rc + (int64_t)col * ldc + I + (int64_t)gc.nx * (J + (int64_t)gc.ny * K), C(0.125) * s);
+}
+
+// The same full weighting for float32 / bfloat16 fine levels with nx divisible by 4: a thread owns
+// the coarse points (2 I2, J) and (2 I2 + 1, J) -- fine x 4 I2 .. 4 I2 + 4, one vector and one
+// scalar per fine row -- and marches along K, reusing the weighted sum of the fine plane 2K + 2 as
+// that of plane 2(K + 1): about 6 loads per coarse point instead of 27.
+template <typename TF, typename TC>
+__global__ void __launch_bounds__(kTX* kTY)
+    k_restrict_v4(Grid3 gf, Grid3 gc, int kchunk, int nkc, const TF* __restrict__ rf, int64_t ldf,
+                  TC* __restrict__ rc, int64_t ldc) {
+    const int I2 = blockIdx.x * kTX + threadIdx.x;
+    const int J = blockIdx.y * kTY + threadIdx.y;
+    const int col = blockIdx.z / nkc;
+    const int kc = blockIdx.z - col * nkc;
+    const int I0 = 2 * I2;
+    if (I0 >= gc.nx || J >= gc.ny) return;
+    const int K0 = kc * kchunk, K1 = min(K0 + kchunk, gc.nz);
+    const int64_t sy = gf.nx, sz = (int64_t)gf.nx * gf.ny;
+    const TF* f = rf + (int64_t)col * ldf;
+    const int fx = 4 * I2;                         // fine x of the vector: 4 I2 .. 4 I2 + 3
+    const bool has4 = fx + 4 < gf.nx;              // fine x 4 I2 + 4 (right neighbour of the second point)
+    const int fy = 2 * J;                          // fine rows 2J .. 2J + 2
+    const bool hasy2 = fy + 2 < gf.ny;
+    // x- and y-weighted sums of fine plane z for the two coarse points
+    auto plane = [&](int z, float& c0, float& c1) {
+        c0 = c1 = 0.f;
+        if (z >= gf.nz) return;
+        const TF* pl = f + (int64_t)z * sz + fx;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            if (dy == 2 && !hasy2) break;
+            const TF* row = pl + (int64_t)(fy + dy) * sy;
+            const float4 v = ld4v(row);
+            const float e = has4 ? (float)ld_as(row + 4) : 0.f;
+            const float a0 = fmaf(0.5f, v.x + v.z, v.y);          // fine 4I2+1 with 4I2, 4I2+2
+            const float a1 = fmaf(0.5f, v.z + e, v.w);            // fine 4I2+3 with 4I2+2, 4I2+4
+            const float wy = dy == 1 ? 1.f : 0.5f;
+            c0 = fmaf(wy, a0, c0);
+            c1 = fmaf(wy, a1, c1);
+        }
+    };
+    const bool two = I0 + 1 < gc.nx;
+    TC* out = rc + (int64_t)col * ldc + I0 + (int64_t)gc.nx * J;
+    float lo0, lo1;
+    plane(2 * K0, lo0, lo1);
+    for (int K = K0; K < K1; ++K) {
+        float m0, m1, h0, h1;
+        plane(2 * K + 1, m0, m1);
+        plane(2 * K + 2, h0, h1);
+        const int64_t o = (int64_t)gc.nx * gc.ny * K;
+        st_as(out + o, 0.125f * (0.5f * (lo0 + h0) + m0));
+        if (two) st_as(out + o + 1, 0.125f * (0.5f * (lo1 + h1) + m1));
+        lo0 = h0;
+        lo1 = h1;
+    }
 }
 
 // Prolongation by coarse cells: cell (Cx, Cy, Cz), 0 <= C <= nc per axis, lies between the
@@ -541,13 +596,17 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
         constexpr uintptr_t al = 4 * sizeof(T);    // one 4-point vector
         if (g.nx % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && (!z || ldz % 4 == 0) &&
             ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % al == 0) {
-            dim3 grid4((unsigned)ceil_div(g.nx / 4, kTX), (unsigned)ceil_div(g.ny, kTY), (unsigned)(nzc * ncols));
+            // rows of fewer than 32 vectors: narrower, taller blocks keep every lane busy
+            const int nx4 = g.nx / 4;
+            const dim3 block4 = nx4 >= 32 ? dim3(32, 4) : (nx4 >= 16 ? dim3(16, 8) : dim3(8, 16));
+            dim3 grid4((unsigned)ceil_div(nx4, (int)block4.x), (unsigned)ceil_div(g.ny, (int)block4.y),
+                       (unsigned)(nzc * ncols));
             if (z)
-                k_stencil_v4<T, true><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
-                                                               (float)c, (const T*)z, ldz, (T*)y, ldy);
+                k_stencil_v4<T, true><<<grid4, block4, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
+                                                                (float)c, (const T*)z, ldz, (T*)y, ldy);
             else
-                k_stencil_v4<T, false><<<grid4, block, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
-                                                                0.f, nullptr, 0, (T*)y, ldy);
+                k_stencil_v4<T, false><<<grid4, block4, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
+                                                                 0.f, nullptr, 0, (T*)y, ldy);
             return;
         }
     }
@@ -563,6 +622,18 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
 template <typename TF, typename TC>
 void restrict_t(const Grid3& gf, const Grid3& gc, int ncols, const void* rf, int64_t ldf, void* rc,
                 int64_t ldc, cudaStream_t st) {
+    if constexpr (!std::is_same<TF, double>::value) {
+        constexpr uintptr_t al = 4 * sizeof(TF);
+        if (gf.nx % 4 == 0 && ldf % 4 == 0 && (uintptr_t)rf % al == 0) {
+            const int kchunk = gc.nz >= 64 ? 8 : (gc.nz >= 16 ? 4 : 2);
+            const int nkc = (int)ceil_div(gc.nz, kchunk);
+            dim3 grid((unsigned)ceil_div(ceil_div(gc.nx, 2), kTX), (unsigned)ceil_div(gc.ny, kTY),
+                      (unsigned)(nkc * ncols));
+            k_restrict_v4<TF, TC><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, kchunk, nkc, (const TF*)rf, ldf, (TC*)rc,
+                                                                   ldc);
+            return;
+        }
+    }
     dim3 grid((unsigned)ceil_div(gc.nx, kTX), (unsigned)ceil_div(gc.ny, kTY), (unsigned)(gc.nz * ncols));
     k_restrict<TF, TC><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, (const TF*)rf, ldf, (TC*)rc, ldc);
 }
