@@ -123,10 +123,12 @@ __global__ void __launch_bounds__(kTX* kTY)
     int64_t p = i0 + sy * (j + (int64_t)g.ny * k0);
     float4 xm = k0 > 0 ? ld4v(xc + p - sz) : zero;
     float4 x0 = ld4v(xc + p);
+    float4 xp = (k0 + 1 < g.nz) ? ld4v(xc + p + sz) : zero;
     const bool hasl = i0 > 0, hasr = i0 + 4 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
     const float a6 = a + 6.f * b;
     for (int k = k0; k < k1; ++k, p += sz) {
-        const float4 xp = (k + 1 < g.nz) ? ld4v(xc + p + sz) : zero;
+        // plane k + 2, one iteration ahead (two planes of x in flight per thread)
+        const float4 xq = (k + 2 < g.nz && k + 1 < k1) ? ld4v(xc + p + 2 * sz) : zero;
         const float l = hasl ? (float)ld_as(xc + p - 1) : 0.f;
         const float r = hasr ? (float)ld_as(xc + p + 4) : 0.f;
         const float4 yd = hasd ? ld4v(xc + p - sy) : zero;
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(kTX* kTY)
         st4v(yc + p, o);
         xm = x0;
         x0 = xp;
+        xp = xq;
     }
 }
 
@@ -198,8 +201,8 @@ template <typename TF, typename TC>
 __global__ void __launch_bounds__(kTX* kTY)
     k_restrict_v4(Grid3 gf, Grid3 gc, int kchunk, int nkc, const TF* __restrict__ rf, int64_t ldf,
                   TC* __restrict__ rc, int64_t ldc) {
-    const int I2 = blockIdx.x * kTX + threadIdx.x;
-    const int J = blockIdx.y * kTY + threadIdx.y;
+    const int I2 = blockIdx.x * blockDim.x + threadIdx.x;   // block shape as for the stencil rows
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int col = blockIdx.z / nkc;
     const int kc = blockIdx.z - col * nkc;
     const int I0 = 2 * I2;
@@ -315,6 +318,81 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
 }
 
+// The same prolongation for float32 / bfloat16 fine levels with nx divisible by 4: a thread owns
+// the fine x-points 4t .. 4t+3 of the fine rows 2cy, 2cy+1 and marches along the cells' z.  Fine
+// x 4t, 4t+1, 4t+2, 4t+3 interpolate the coarse x-points 2t, 2t+1, 2t+2 (1-based; one 2-vector
+// and one scalar per coarse row); each coarse row is interpolated in x once and the two rows and
+// two planes of a cell are then combined in y and z, so a fine vector costs one load and one
+// store.
+__device__ __forceinline__ float2 ld2v(const float* q) { return __ldg(reinterpret_cast<const float2*>(q)); }
+__device__ __forceinline__ float2 ld2v(const __nv_bfloat16* q) {
+    const unsigned u = __ldg(reinterpret_cast<const unsigned*>(q));
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+template <typename TC, typename TF>
+__global__ void __launch_bounds__(kTX* kTY)
+    k_prolong_v4(Grid3 gf, Grid3 gc, int zchunk, int nzc, const TC* __restrict__ ec, int64_t ldc,
+                 TF* __restrict__ ef, int64_t ldf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int col = blockIdx.z / nzc;
+    const int kc = blockIdx.z - col * nzc;
+    if (4 * t >= gf.nx || 2 * cy >= gf.ny) return;
+    const int ncz = (gf.nz + 1) / 2;               // cells along z that own fine planes
+    const int z0 = kc * zchunk, z1 = min(z0 + zchunk, ncz);
+    const TC* c = ec + (int64_t)col * ldc;
+    TF* f = ef + (int64_t)col * ldf;
+    const int64_t csz = (int64_t)gc.nx * gc.ny;
+    const int64_t fsy = gf.nx, fsz = (int64_t)gf.nx * gf.ny;
+    // coarse row (Y, Z) (1-based, zero outside 1..nc) interpolated to the fine x 4t .. 4t+3
+    auto xrow = [&](int Y, int Z, float (&v)[4]) {
+        if (Y < 1 || Y > gc.ny || Z < 1 || Z > gc.nz) {
+            v[0] = v[1] = v[2] = v[3] = 0.f;
+            return;
+        }
+        const TC* row = c + (int64_t)gc.nx * (Y - 1) + csz * (Z - 1);
+        const float2 ab = ld2v(row + 2 * t);       // X = 2t+1, 2t+2
+        const float m = t > 0 ? (float)ld_as(row + 2 * t - 1) : 0.f;   // X = 2t
+        v[0] = 0.5f * (m + ab.x);
+        v[1] = ab.x;
+        v[2] = 0.5f * (ab.x + ab.y);
+        v[3] = ab.y;
+    };
+    float lo[2][4], hi[2][4];                     // [Y = cy, cy+1][x] on planes Z = cz (lo), cz+1 (hi)
+    xrow(cy, z0, lo[0]);
+    xrow(cy + 1, z0, lo[1]);
+    for (int cz = z0; cz < z1; ++cz) {
+        xrow(cy, cz + 1, hi[0]);
+        xrow(cy + 1, cz + 1, hi[1]);
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+            const int fz = 2 * cz + dz;
+            if (fz >= gf.nz) break;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int fy = 2 * cy + dy;
+                if (fy >= gf.ny) break;
+                TF* q = f + fsz * fz + fsy * fy + 4 * t;
+                const float4 old = ld4v(q);
+                const float o4[4] = {old.x, old.y, old.z, old.w};
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float p0 = dz ? hi[0][e] : 0.5f * (lo[0][e] + hi[0][e]);
+                    const float p1 = dz ? hi[1][e] : 0.5f * (lo[1][e] + hi[1][e]);
+                    o[e] = o4[e] + (dy ? p1 : 0.5f * (p0 + p1));
+                }
+                st4v(q, o);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) lo[r][e] = hi[r][e];
+    }
+}
+
 // Coarsest-level exact solve.  The 7-point Dirichlet operator s*(6u - nb) on an
 // nx x ny x nz box has the orthonormal eigenvectors Qz (x) Qy (x) Qx with
 // Q_d[a][i] = sqrt(2/(n_d+1)) sin(pi (a+1)(i+1)/(n_d+1)) (symmetric, Q_d^2 = I) and the
@@ -396,6 +474,8 @@ __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const T*
 // same steps as the multi-kernel path -- fused first two pre-sweeps, Jacobi sweeps, residual,
 // full-weighting restriction, exact sine-transform solve on the coarsest level, trilinear
 // prolongation, post-sweeps -- separated by block barriers instead of kernel launches.
+constexpr int kSmallThreads = 1024;   // block of the fused small-level V-cycle
+
 struct SmallLevels {
     int nl;
     Grid3 g[kFuseMaxLevels];
@@ -403,31 +483,56 @@ struct SmallLevels {
     int off[kFuseMaxLevels];    // element offset of level l's three vectors (r, e, t)
 };
 
+// Threads of the block over the (i, j) lines of a level: when the block has more threads than a
+// plane has lines, each line is split into nsplit runs along k.  A thread marches its run,
+// carrying the k-1 / k / k+1 values in registers (one division per line instead of three per
+// point).
+struct SmLines {
+    int P, nsplit, kper;
+    __device__ SmLines(const Grid3& g) {
+        P = g.nx * g.ny;
+        nsplit = P >= (int)blockDim.x ? 1 : min(g.nz, (int)blockDim.x / P);
+        kper = (g.nz + nsplit - 1) / nsplit;
+    }
+};
+
 template <typename C>
 __device__ void sm_axpby(const Grid3& g, C a, C b, const C* x, C c, const C* z, C* y) {
-    const int nx = g.nx, ny = g.ny, nz = g.nz, n = nx * ny * nz, sy = nx, sz = nx * ny;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int i = p % nx, j = (p / nx) % ny, k = p / sz;
-        const C x0 = x[p];
-        const C xm = k > 0 ? x[p - sz] : C(0), xp = k + 1 < nz ? x[p + sz] : C(0);
-        C v;
-        if constexpr (sizeof(C) == 8) {
-            C nb = xm + xp;
-            if (i > 0) nb += x[p - 1];
-            if (i + 1 < nx) nb += x[p + 1];
-            if (j > 0) nb += x[p - sy];
-            if (j + 1 < ny) nb += x[p + sy];
-            v = fma(b, nb, a * x0);
-        } else {
-            C d = (x0 - xm) + (x0 - xp);
-            d += i > 0 ? x0 - x[p - 1] : x0;
-            d += i + 1 < nx ? x0 - x[p + 1] : x0;
-            d += j > 0 ? x0 - x[p - sy] : x0;
-            d += j + 1 < ny ? x0 - x[p + sy] : x0;
-            v = fma(-b, d, (a + C(6) * b) * x0);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, sy = nx;
+    const SmLines L(g);
+    const int sz = L.P;
+    for (int t = threadIdx.x; t < L.P * L.nsplit; t += blockDim.x) {
+        const int part = t / L.P, q = t - part * L.P;
+        const int j = q / nx, i = q - j * nx;
+        const int k0 = part * L.kper, k1 = min(nz, k0 + L.kper);
+        if (k0 >= k1) continue;
+        int p = q + k0 * sz;
+        C xm = k0 > 0 ? x[p - sz] : C(0);
+        C x0 = x[p];
+        const bool hl = i > 0, hr = i + 1 < nx, hd = j > 0, hu = j + 1 < ny;
+        for (int k = k0; k < k1; ++k, p += sz) {
+            const C xp = k + 1 < nz ? x[p + sz] : C(0);
+            C v;
+            if constexpr (sizeof(C) == 8) {
+                C nb = xm + xp;
+                if (hl) nb += x[p - 1];
+                if (hr) nb += x[p + 1];
+                if (hd) nb += x[p - sy];
+                if (hu) nb += x[p + sy];
+                v = fma(b, nb, a * x0);
+            } else {
+                C d = (x0 - xm) + (x0 - xp);
+                d += hl ? x0 - x[p - 1] : x0;
+                d += hr ? x0 - x[p + 1] : x0;
+                d += hd ? x0 - x[p - sy] : x0;
+                d += hu ? x0 - x[p + sy] : x0;
+                v = fma(-b, d, (a + C(6) * b) * x0);
+            }
+            if (z) v = fma(c, z[p], v);
+            y[p] = v;
+            xm = x0;
+            x0 = xp;
         }
-        if (z) v = fma(c, z[p], v);
-        y[p] = v;
     }
     __syncthreads();
 }
@@ -477,31 +582,37 @@ __device__ __forceinline__ void sm_taps(int f0, int nc, int& i0, int& i1, float&
 
 template <typename C>
 __device__ void sm_prolong_add(const Grid3& gf, const Grid3& gc, const C* ec, C* ef) {
-    const int nf = gf.n();
-    for (int p = threadIdx.x; p < nf; p += blockDim.x) {
-        const int i = p % gf.nx, j = (p / gf.nx) % gf.ny, k = p / (gf.nx * gf.ny);
-        int xi[2], yi[2], zi[2];
-        float xw[2], yw[2], zw[2];
+    const SmLines L(gf);
+    for (int t = threadIdx.x; t < L.P * L.nsplit; t += blockDim.x) {
+        const int part = t / L.P, q = t - part * L.P;
+        const int j = q / gf.nx, i = q - j * gf.nx;
+        const int k0 = part * L.kper, k1 = min(gf.nz, k0 + L.kper);
+        int xi[2], yi[2];
+        float xw[2], yw[2];
         sm_taps(i, gc.nx, xi[0], xi[1], xw[0], xw[1]);
         sm_taps(j, gc.ny, yi[0], yi[1], yw[0], yw[1]);
-        sm_taps(k, gc.nz, zi[0], zi[1], zw[0], zw[1]);
-        C sacc = 0;
+        for (int k = k0; k < k1; ++k) {
+            int zi[2];
+            float zw[2];
+            sm_taps(k, gc.nz, zi[0], zi[1], zw[0], zw[1]);
+            C sacc = 0;
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const C w = C(zw[a]) * C(yw[b]);
-                const int row = gc.nx * (yi[b] + gc.ny * zi[a]);
+                for (int b = 0; b < 2; ++b) {
+                    const C w = C(zw[a]) * C(yw[b]);
+                    const int row = gc.nx * (yi[b] + gc.ny * zi[a]);
 #pragma unroll
-                for (int d = 0; d < 2; ++d) sacc = fma(w * C(xw[d]), ec[row + xi[d]], sacc);
-            }
-        ef[p] += sacc;
+                    for (int d = 0; d < 2; ++d) sacc = fma(w * C(xw[d]), ec[row + xi[d]], sacc);
+                }
+            ef[q + k * L.P] += sacc;
+        }
     }
     __syncthreads();
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kSmallThreads)
     k_vcycle_small(SmallLevels L, double omega, int nu_pre, int nu_post, const double* __restrict__ tab,
                    const T* __restrict__ r, int64_t ldr, T* __restrict__ e, int64_t lde) {
     extern __shared__ __align__(16) double smd[];
@@ -598,15 +709,17 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
             ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % al == 0) {
             // rows of fewer than 32 vectors: narrower, taller blocks keep every lane busy
             const int nx4 = g.nx / 4;
+            const int zc4 = g.nz >= 128 ? 8 : zc;   // shorter runs on the large grids: more blocks per wave
+            const int nzc4 = (int)ceil_div(g.nz, zc4);
             const dim3 block4 = nx4 >= 32 ? dim3(32, 4) : (nx4 >= 16 ? dim3(16, 8) : dim3(8, 16));
             dim3 grid4((unsigned)ceil_div(nx4, (int)block4.x), (unsigned)ceil_div(g.ny, (int)block4.y),
-                       (unsigned)(nzc * ncols));
+                       (unsigned)(nzc4 * ncols));
             if (z)
-                k_stencil_v4<T, true><<<grid4, block4, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
+                k_stencil_v4<T, true><<<grid4, block4, 0, st>>>(g, zc4, nzc4, (float)a, (float)b, (const T*)x, ldx,
                                                                 (float)c, (const T*)z, ldz, (T*)y, ldy);
             else
-                k_stencil_v4<T, false><<<grid4, block4, 0, st>>>(g, zc, nzc, (float)a, (float)b, (const T*)x, ldx,
-                                                                 0.f, nullptr, 0, (T*)y, ldy);
+                k_stencil_v4<T, false><<<grid4, block4, 0, st>>>(g, zc4, nzc4, (float)a, (float)b, (const T*)x,
+                                                                 ldx, 0.f, nullptr, 0, (T*)y, ldy);
             return;
         }
     }
@@ -627,10 +740,11 @@ void restrict_t(const Grid3& gf, const Grid3& gc, int ncols, const void* rf, int
         if (gf.nx % 4 == 0 && ldf % 4 == 0 && (uintptr_t)rf % al == 0) {
             const int kchunk = gc.nz >= 64 ? 8 : (gc.nz >= 16 ? 4 : 2);
             const int nkc = (int)ceil_div(gc.nz, kchunk);
-            dim3 grid((unsigned)ceil_div(ceil_div(gc.nx, 2), kTX), (unsigned)ceil_div(gc.ny, kTY),
+            const int pairs = (int)ceil_div(gc.nx, 2);
+            const dim3 block = pairs >= 32 ? dim3(32, 4) : (pairs >= 16 ? dim3(16, 8) : dim3(8, 16));
+            dim3 grid((unsigned)ceil_div(pairs, (int)block.x), (unsigned)ceil_div(gc.ny, (int)block.y),
                       (unsigned)(nkc * ncols));
-            k_restrict_v4<TF, TC><<<grid, dim3(kTX, kTY), 0, st>>>(gf, gc, kchunk, nkc, (const TF*)rf, ldf, (TC*)rc,
-                                                                   ldc);
+            k_restrict_v4<TF, TC><<<grid, block, 0, st>>>(gf, gc, kchunk, nkc, (const TF*)rf, ldf, (TC*)rc, ldc);
             return;
         }
     }
@@ -641,6 +755,19 @@ void restrict_t(const Grid3& gf, const Grid3& gc, int ncols, const void* rf, int
 template <typename TC, typename TF>
 void prolong_t(const Grid3& gf, const Grid3& gc, int ncols, const void* ec, int64_t ldc, void* ef, int64_t ldf,
                cudaStream_t st) {
+    if constexpr (!std::is_same<TF, double>::value && !std::is_same<TC, double>::value) {
+        if (gf.nx % 4 == 0 && ldf % 4 == 0 && ldc % 2 == 0 && (uintptr_t)ef % (4 * sizeof(TF)) == 0 &&
+            (uintptr_t)ec % (2 * sizeof(TC)) == 0) {
+            const int quads = gf.nx / 4, pairs = (gf.ny + 1) / 2, ncz = (gf.nz + 1) / 2;
+            const int zc = ncz >= 64 ? 4 : (ncz >= 8 ? 2 : 1);
+            const int nzc = (int)ceil_div(ncz, zc);
+            const dim3 block = quads >= 32 ? dim3(32, 4) : (quads >= 16 ? dim3(16, 8) : dim3(8, 16));
+            dim3 grid((unsigned)ceil_div(quads, (int)block.x), (unsigned)ceil_div(pairs, (int)block.y),
+                      (unsigned)(nzc * ncols));
+            k_prolong_v4<TC, TF><<<grid, block, 0, st>>>(gf, gc, zc, nzc, (const TC*)ec, ldc, (TF*)ef, ldf);
+            return;
+        }
+    }
     const int zc = zchunk_for(gc.nz + 1);
     const int nzc = (int)ceil_div(gc.nz + 1, zc);
     dim3 grid((unsigned)ceil_div(gc.nx + 1, kTX), (unsigned)ceil_div(gc.ny + 1, kTY), (unsigned)(nzc * ncols));
@@ -765,9 +892,9 @@ void launch_vcycle_small(const Grid3* g, const double* scales, int nl, double om
         attr[dev][t] = true;
     }
     switch (t) {
-        case DT_F64: k_vcycle_small<double, double><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const double*)r, ldr, (double*)e, lde); break;
-        case DT_F32: k_vcycle_small<float, float><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const float*)r, ldr, (float*)e, lde); break;
-        case DT_BF16: k_vcycle_small<__nv_bfloat16, float><<<ncols, 512, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const __nv_bfloat16*)r, ldr, (__nv_bfloat16*)e, lde); break;
+        case DT_F64: k_vcycle_small<double, double><<<ncols, kSmallThreads, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const double*)r, ldr, (double*)e, lde); break;
+        case DT_F32: k_vcycle_small<float, float><<<ncols, kSmallThreads, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const float*)r, ldr, (float*)e, lde); break;
+        case DT_BF16: k_vcycle_small<__nv_bfloat16, float><<<ncols, kSmallThreads, smem, st>>>(L, omega, nu_pre, nu_post, tables, (const __nv_bfloat16*)r, ldr, (__nv_bfloat16*)e, lde); break;
     }
     LG_CHECK_LAUNCH();
 }
