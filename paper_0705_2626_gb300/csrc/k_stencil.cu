@@ -442,6 +442,21 @@ __device__ void sine_pass(const Grid3& g, int ax, const double* __restrict__ Q,
     __syncthreads();
 }
 
+// The same pass with Q in shared memory (plain loads; the same order of operations).
+__device__ void sine_pass_sm(const Grid3& g, int ax, const double* Q, const double* in, double* out) {
+    const int n = g.nx * g.ny * g.nz;
+    const int na = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+    const int stride = ax == 0 ? 1 : (ax == 1 ? g.nx : g.nx * g.ny);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int a = (p / stride) % na;
+        const int base = p - a * stride;
+        double s = 0.0;
+        for (int i = 0; i < na; ++i) s = fma(Q[a * na + i], in[base + i * stride], s);
+        out[p] = s;
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const T* __restrict__ r,
                                int64_t ldr, T* __restrict__ e, int64_t lde) {
@@ -474,7 +489,7 @@ __global__ void k_coarse_solve(Grid3 g, const double* __restrict__ tab, const T*
 // same steps as the multi-kernel path -- fused first two pre-sweeps, Jacobi sweeps, residual,
 // full-weighting restriction, exact sine-transform solve on the coarsest level, trilinear
 // prolongation, post-sweeps -- separated by block barriers instead of kernel launches.
-constexpr int kSmallThreads = 1024;   // block of the fused small-level V-cycle
+constexpr int kSmallThreads = 512;    // block of the fused small-level V-cycle (1024 measured slower)
 
 struct SmallLevels {
     int nl;
@@ -497,7 +512,8 @@ struct SmLines {
 };
 
 template <typename C>
-__device__ void sm_axpby(const Grid3& g, C a, C b, const C* x, C c, const C* z, C* y) {
+__device__ void sm_axpby(const Grid3& g, C a, C b, const C* __restrict__ x, C c, const C* __restrict__ z,
+                         C* __restrict__ y) {
     const int nx = g.nx, ny = g.ny, nz = g.nz, sy = nx;
     const SmLines L(g);
     const int sz = L.P;
@@ -538,7 +554,7 @@ __device__ void sm_axpby(const Grid3& g, C a, C b, const C* x, C c, const C* z, 
 }
 
 template <typename C>
-__device__ void sm_restrict(const Grid3& gf, const Grid3& gc, const C* f, C* rc) {
+__device__ void sm_restrict(const Grid3& gf, const Grid3& gc, const C* __restrict__ f, C* __restrict__ rc) {
     const int nc = gc.n();
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
         const int I = q % gc.nx, J = (q / gc.nx) % gc.ny, K = q / (gc.nx * gc.ny);
@@ -581,7 +597,7 @@ __device__ __forceinline__ void sm_taps(int f0, int nc, int& i0, int& i1, float&
 }
 
 template <typename C>
-__device__ void sm_prolong_add(const Grid3& gf, const Grid3& gc, const C* ec, C* ef) {
+__device__ void sm_prolong_add(const Grid3& gf, const Grid3& gc, const C* __restrict__ ec, C* __restrict__ ef) {
     const SmLines L(gf);
     for (int t = threadIdx.x; t < L.P * L.nsplit; t += blockDim.x) {
         const int part = t / L.P, q = t - part * L.P;
@@ -618,12 +634,18 @@ __global__ void __launch_bounds__(kSmallThreads)
     extern __shared__ __align__(16) double smd[];
     const Grid3 gc = L.g[L.nl - 1];
     const int ncs = gc.n();
-    double* u = smd;                     // sine-transform scratch of the coarsest level
-    double* v = smd + ncs;
-    C* sm = reinterpret_cast<C*>(smd + 2 * ncs);
+    const int ntab = gc.nx * gc.nx + gc.ny * gc.ny + gc.nz * gc.nz;
+    double* tq = smd;                    // the coarsest level's sine tables Qx, Qy, Qz
+    double* u = smd + ntab;              // sine-transform scratch of the coarsest level
+    double* v = u + ncs;
+    C* sm = reinterpret_cast<C*>(v + ncs);
     const int col = blockIdx.x;
     const int n0 = L.g[0].n();
     C* R0 = sm + L.off[0];
+    const double* lam = tab + ntab;      // eigenvalues (global memory; a thread's own one prefetched)
+    const bool lam_in_reg = ncs <= (int)blockDim.x;
+    const double lam_r = lam_in_reg && (int)threadIdx.x < ncs ? __ldg(lam + threadIdx.x) : 1.0;
+    for (int p = threadIdx.x; p < ntab; p += blockDim.x) tq[p] = __ldg(tab + p);
     for (int p = threadIdx.x; p < n0; p += blockDim.x) R0[p] = C(ld_as(r + (int64_t)col * ldr + p));
     __syncthreads();
     C* fin[kFuseMaxLevels];    // final e of each level
@@ -651,20 +673,19 @@ __global__ void __launch_bounds__(kSmallThreads)
     {   // coarsest: e = Q diag(1/lambda) Q r
         const C* Rc = sm + L.off[L.nl - 1];
         C* Ec = sm + L.off[L.nl - 1] + ncs;
-        const double* Qx = tab;
+        const double* Qx = tq;
         const double* Qy = Qx + gc.nx * gc.nx;
         const double* Qz = Qy + gc.ny * gc.ny;
-        const double* lam = Qz + gc.nz * gc.nz;
         for (int p = threadIdx.x; p < ncs; p += blockDim.x) u[p] = (double)Rc[p];
         __syncthreads();
-        sine_pass(gc, 0, Qx, u, v);
-        sine_pass(gc, 1, Qy, v, u);
-        sine_pass(gc, 2, Qz, u, v);
-        for (int p = threadIdx.x; p < ncs; p += blockDim.x) v[p] /= lam[p];
+        sine_pass_sm(gc, 0, Qx, u, v);
+        sine_pass_sm(gc, 1, Qy, v, u);
+        sine_pass_sm(gc, 2, Qz, u, v);
+        for (int p = threadIdx.x; p < ncs; p += blockDim.x) v[p] /= lam_in_reg ? lam_r : __ldg(lam + p);
         __syncthreads();
-        sine_pass(gc, 0, Qx, v, u);
-        sine_pass(gc, 1, Qy, u, v);
-        sine_pass(gc, 2, Qz, v, u);
+        sine_pass_sm(gc, 0, Qx, v, u);
+        sine_pass_sm(gc, 1, Qy, u, v);
+        sine_pass_sm(gc, 2, Qz, v, u);
         for (int p = threadIdx.x; p < ncs; p += blockDim.x) Ec[p] = C(u[p]);
         __syncthreads();
         fin[L.nl - 1] = Ec;
@@ -864,7 +885,9 @@ size_t vcycle_small_smem(const Grid3* g, int nl, DType t) {
     const size_t cs = t == DT_F64 ? 8 : 4;
     size_t elems = 0;
     for (int l = 0; l < nl; ++l) elems += 3 * (size_t)g[l].n();
-    return 2 * (size_t)g[nl - 1].n() * sizeof(double) + elems * cs;
+    const Grid3& c = g[nl - 1];
+    const size_t q = (size_t)c.nx * c.nx + (size_t)c.ny * c.ny + (size_t)c.nz * c.nz;   // staged sine tables
+    return (2 * (size_t)c.n() + q) * sizeof(double) + elems * cs;
 }
 
 void launch_vcycle_small(const Grid3* g, const double* scales, int nl, double omega, int nu_pre, int nu_post,
