@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kTX* kTY)
 }
 
 // Float32 or bfloat16 storage with nx divisible by 4: each thread owns 4 consecutive points of an
-// x-row (one 16- or 8-byte vector) and marches along k, so a point costs about 1.25 load
+// x-row (one 16- or 8-byte vector) over a run of planes along k, so a point costs about 1.25 load
 // instructions instead of 6.  Float32 arithmetic, the difference form of the branch above with
 // the neighbours added in the same order.
 __device__ __forceinline__ float4 ld4v(const float* q) { return __ldg(reinterpret_cast<const float4*>(q)); }
@@ -102,10 +102,13 @@ __device__ __forceinline__ void st4v(__nv_bfloat16* q, const float (&o)[4]) {
     *reinterpret_cast<uint2*>(q) = u;
 }
 
-template <typename T, bool HAS_Z>
+// A thread's run of ZC planes issues all of its loads -- the ZC + 2 planes of its x vector, the
+// y-neighbour vectors, the x-neighbour scalars and the z vectors -- before any arithmetic, so the
+// run waits for one memory round trip instead of one per plane.
+template <typename T, bool HAS_Z, int ZC>
 __global__ void __launch_bounds__(kTX* kTY)
-    k_stencil_v4(Grid3 g, int zchunk, int nzc, float a, float b, const T* __restrict__ x, int64_t ldx,
-                 float c, const T* __restrict__ z, int64_t ldz, T* __restrict__ y, int64_t ldy) {
+    k_stencil_v4(Grid3 g, int nzc, float a, float b, const T* __restrict__ x, int64_t ldx, float c,
+                 const T* __restrict__ z, int64_t ldz, T* __restrict__ y, int64_t ldy) {
     const int nx4 = g.nx >> 2;
     const int i4 = blockIdx.x * blockDim.x + threadIdx.x;   // block (32, 4), or (16, 8) / (8, 16) for short rows
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -113,31 +116,40 @@ __global__ void __launch_bounds__(kTX* kTY)
     const int kc = blockIdx.z - col * nzc;
     if (i4 >= nx4 || j >= g.ny) return;
     const int i0 = 4 * i4;
-    const int k0 = kc * zchunk;
-    const int k1 = min(k0 + zchunk, g.nz);
+    const int k0 = kc * ZC;
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     const T* xc = x + (int64_t)col * ldx;
     const T* zc = HAS_Z ? z + (int64_t)col * ldz : nullptr;
     T* yc = y + (int64_t)col * ldy;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    int64_t p = i0 + sy * (j + (int64_t)g.ny * k0);
-    float4 xm = k0 > 0 ? ld4v(xc + p - sz) : zero;
-    float4 x0 = ld4v(xc + p);
-    float4 xp = (k0 + 1 < g.nz) ? ld4v(xc + p + sz) : zero;
+    const int64_t p0 = i0 + sy * (j + (int64_t)g.ny * k0);
     const bool hasl = i0 > 0, hasr = i0 + 4 < g.nx, hasd = j > 0, hasu = j + 1 < g.ny;
+    float4 xs[ZC + 2], yd[ZC], yu[ZC], zz[ZC];     // xs[q]: plane k0 - 1 + q
+    float ls[ZC], rs[ZC];
+#pragma unroll
+    for (int q = 0; q < ZC + 2; ++q) {
+        const int k = k0 - 1 + q;
+        xs[q] = (k >= 0 && k < g.nz) ? ld4v(xc + p0 + (int64_t)(q - 1) * sz) : zero;
+    }
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+        const bool in = k0 + q < g.nz;
+        const int64_t p = p0 + (int64_t)q * sz;
+        yd[q] = in && hasd ? ld4v(xc + p - sy) : zero;
+        yu[q] = in && hasu ? ld4v(xc + p + sy) : zero;
+        ls[q] = in && hasl ? (float)ld_as(xc + p - 1) : 0.f;
+        rs[q] = in && hasr ? (float)ld_as(xc + p + 4) : 0.f;
+        zz[q] = in && HAS_Z ? ld4v(zc + p) : zero;
+    }
     const float a6 = a + 6.f * b;
-    for (int k = k0; k < k1; ++k, p += sz) {
-        // plane k + 2, one iteration ahead (two planes of x in flight per thread)
-        const float4 xq = (k + 2 < g.nz && k + 1 < k1) ? ld4v(xc + p + 2 * sz) : zero;
-        const float l = hasl ? (float)ld_as(xc + p - 1) : 0.f;
-        const float r = hasr ? (float)ld_as(xc + p + 4) : 0.f;
-        const float4 yd = hasd ? ld4v(xc + p - sy) : zero;
-        const float4 yu = hasu ? ld4v(xc + p + sy) : zero;
-        const float4 zz = HAS_Z ? ld4v(zc + p) : zero;
-        const float cx[6] = {l, x0.x, x0.y, x0.z, x0.w, r};
+#pragma unroll
+    for (int q = 0; q < ZC; ++q) {
+        if (k0 + q >= g.nz) break;
+        const float4 xm = xs[q], x0 = xs[q + 1], xp = xs[q + 2];
+        const float cx[6] = {ls[q], x0.x, x0.y, x0.z, x0.w, rs[q]};
         const float m_[4] = {xm.x, xm.y, xm.z, xm.w}, p_[4] = {xp.x, xp.y, xp.z, xp.w};
-        const float d_[4] = {yd.x, yd.y, yd.z, yd.w}, u_[4] = {yu.x, yu.y, yu.z, yu.w};
-        const float z_[4] = {zz.x, zz.y, zz.z, zz.w};
+        const float d_[4] = {yd[q].x, yd[q].y, yd[q].z, yd[q].w}, u_[4] = {yu[q].x, yu[q].y, yu[q].z, yu[q].w};
+        const float z_[4] = {zz[q].x, zz[q].y, zz[q].z, zz[q].w};
         float o[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -151,10 +163,7 @@ __global__ void __launch_bounds__(kTX* kTY)
             if (HAS_Z) v = fmaf(c, z_[e], v);
             o[e] = v;
         }
-        st4v(yc + p, o);
-        xm = x0;
-        x0 = xp;
-        xp = xq;
+        st4v(yc + p0 + (int64_t)q * sz, o);
     }
 }
 
@@ -730,17 +739,24 @@ void stencil_t(const Grid3& g, int ncols, double a, double b, const void* x, int
             ((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) % al == 0) {
             // rows of fewer than 32 vectors: narrower, taller blocks keep every lane busy
             const int nx4 = g.nx / 4;
-            const int zc4 = g.nz >= 128 ? 8 : zc;   // shorter runs on the large grids: more blocks per wave
-            const int nzc4 = (int)ceil_div(g.nz, zc4);
+            const bool four = g.nz >= 64;            // 4-plane runs on large grids, 2-plane runs below
+            const int nzc4 = (int)ceil_div(g.nz, four ? 4 : 2);
             const dim3 block4 = nx4 >= 32 ? dim3(32, 4) : (nx4 >= 16 ? dim3(16, 8) : dim3(8, 16));
             dim3 grid4((unsigned)ceil_div(nx4, (int)block4.x), (unsigned)ceil_div(g.ny, (int)block4.y),
                        (unsigned)(nzc4 * ncols));
-            if (z)
-                k_stencil_v4<T, true><<<grid4, block4, 0, st>>>(g, zc4, nzc4, (float)a, (float)b, (const T*)x, ldx,
-                                                                (float)c, (const T*)z, ldz, (T*)y, ldy);
+            const float fa = (float)a, fb = (float)b, fc = (float)c;
+            if (z && four)
+                k_stencil_v4<T, true, 4><<<grid4, block4, 0, st>>>(g, nzc4, fa, fb, (const T*)x, ldx, fc, (const T*)z, ldz,
+                                                                   (T*)y, ldy);
+            else if (z)
+                k_stencil_v4<T, true, 2><<<grid4, block4, 0, st>>>(g, nzc4, fa, fb, (const T*)x, ldx, fc, (const T*)z, ldz,
+                                                                   (T*)y, ldy);
+            else if (four)
+                k_stencil_v4<T, false, 4><<<grid4, block4, 0, st>>>(g, nzc4, fa, fb, (const T*)x, ldx, 0.f, nullptr, 0,
+                                                                    (T*)y, ldy);
             else
-                k_stencil_v4<T, false><<<grid4, block4, 0, st>>>(g, zc4, nzc4, (float)a, (float)b, (const T*)x,
-                                                                 ldx, 0.f, nullptr, 0, (T*)y, ldy);
+                k_stencil_v4<T, false, 2><<<grid4, block4, 0, st>>>(g, nzc4, fa, fb, (const T*)x, ldx, 0.f, nullptr, 0,
+                                                                    (T*)y, ldy);
             return;
         }
     }
