@@ -266,6 +266,13 @@ int lobpcg_op_random_block(lobpcg_t* h, uint64_t seed, int m, double* X, int64_t
 int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx,
                       double* Y, int64_t ldy);
 
+/* The mixed form's SpMV (Algorithm step 12 on a LOBPCG_MIXED handle): Y = A X
+ * for ncols float32 device columns (n rows, leading dimensions ldx, ldy >= n),
+ * float32 arithmetic, each point's six neighbour differences summed before the
+ * scaling.  X and Y must not overlap.  ERR_ARG on a LOBPCG_FP64 handle. */
+int lobpcg_op_stencil_f32(lobpcg_t* h, int ncols, const float* X, int64_t ldx,
+                          float* Y, int64_t ldy);
+
 /* E = T R for `ncols` columns (Algorithm step 9; T = I copies): device R, E,
  * which must not overlap.  Needs a LOBPCG_FP64 handle. */
 int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,

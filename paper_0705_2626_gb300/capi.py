@@ -64,6 +64,7 @@ _SIGNATURES = {
     "lobpcg_op_stencil": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p, c_int64]),
     "lobpcg_op_precond": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p, c_int64]),
     "lobpcg_op_precond_f32": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p, c_int64]),
+    "lobpcg_op_stencil_f32": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p, c_int64]),
     "lobpcg_op_residual": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int), c_void_p, c_void_p, c_int64,
                                    c_void_p, c_void_p, c_int64, c_void_p]),
     "lobpcg_op_gram": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -182,6 +183,10 @@ def lobpcg_op_precond(h, ncols, R, ldr, E, lde):
 
 def lobpcg_op_precond_f32(h, ncols, R, ldr, E, lde):
     return _call("lobpcg_op_precond_f32", h, ncols, R, ldr, E, lde)
+
+
+def lobpcg_op_stencil_f32(h, ncols, X, ldx, Y, ldy):
+    return _call("lobpcg_op_stencil_f32", h, ncols, X, ldx, Y, ldy)
 
 
 def lobpcg_op_residual(h, ncols, cols, X, AX, ld, lam, W, ldw, norms):

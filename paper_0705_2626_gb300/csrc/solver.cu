@@ -1332,6 +1332,20 @@ int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx, doub
     });
 }
 
+int lobpcg_op_stencil_f32(lobpcg_t* h, int ncols, const float* X, int64_t ldx, float* Y, int64_t ldy) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        LG_REQUIRE(X && Y && ncols >= 0 && valid_ld(ldx, n) && valid_ld(ldy, n), LOBPCG_ERR_ARG,
+                   "invalid stencil arguments");
+        LG_REQUIRE(h->precision == LOBPCG_MIXED && !h->varcoef, LOBPCG_ERR_ARG,
+                   "lobpcg_op_stencil_f32 needs a LOBPCG_MIXED handle");
+        spmv(h, ncols, DT_F32, X, ldx, Y, ldy);
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        return LOBPCG_OK;
+    });
+}
+
 int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr, double* E, int64_t lde) {
     return guarded(h, [&] {
         require_op(h);

@@ -53,6 +53,37 @@ def test_stencil_matches_oracle(dims, m):
     assert torch.isnan(Yd[:, n:]).all()          # padding rows untouched
 
 
+@pytest.mark.parametrize("dims,m", [((24, 13, 11), 3), ((8, 8, 70), 2), ((36, 17, 65), 5), ((4, 1, 1), 1),
+                                    ((33, 33, 33), 4), ((128, 128, 128), 16)])
+@pytest.mark.parametrize("ld_kind", ["vec", "odd"])
+def test_stencil_f32_matches_oracle(dims, m, ld_kind):
+    """The mixed form's float32 SpMV against the float64 operator on the same float32 inputs.
+    With nx divisible by 4 and a leading dimension divisible by 4 the float4-row kernel runs
+    (ragged runs of 2 or 4 planes, odd ny / nz here); an odd leading dimension takes the scalar
+    kernel.  Bound: a few float32 roundings of the six neighbour differences, their sum and the
+    scaling, 16 eps32 * s * 12 * max|x|."""
+    s = Solver(dims, scale=3.25, precond="none", precision="mixed")
+    n = s.n
+    ld = (n + 3) // 4 * 4 + 4 if ld_kind == "vec" else n + 7
+    X = np.random.default_rng(3).uniform(-1, 1, (n, m)).astype(np.float32)
+    Xd = torch.full((m, ld), float("nan"), dtype=torch.float32, device="cuda")
+    Xd[:, :n] = torch.tensor(np.ascontiguousarray(X.T), device="cuda")
+    Yd = torch.full((m, ld), float("nan"), dtype=torch.float32, device="cuda")
+    assert capi.lobpcg_op_stencil_f32(s.h, m, ptr(Xd), ld, ptr(Yd), ld) == capi.OK
+    got = Yd[:, :n].cpu().numpy().T.astype(np.float64)
+    want = laplace.apply(X.astype(np.float64), dims, 3.25)
+    bound = 16 * np.finfo(np.float32).eps * 3.25 * 12 * np.max(np.abs(X))
+    assert np.max(np.abs(got - want)) <= bound
+    assert torch.isnan(Yd[:, n:]).all()          # padding rows untouched
+    s.close()
+
+
+def test_stencil_f32_needs_mixed_handle():
+    s = make((8, 8, 8), scale=1.0, precond="none")
+    X = torch.zeros((1, 512), dtype=torch.float32, device="cuda")
+    assert capi.lobpcg_op_stencil_f32(s.h, 1, ptr(X), 512, ptr(X), 512) == capi.ERR_ARG
+
+
 @pytest.mark.parametrize("dims,levels,m", [((7, 7, 7), 1, 3), ((8, 8, 8), 2, 2), ((16, 16, 16), 3, 4),
                                            ((15, 17, 13), 3, 3), ((48, 48, 48), 4, 8),
                                            ((128, 128, 128), 6, 16)])
@@ -69,7 +100,7 @@ def test_vcycle_matches_oracle(dims, levels, m):
 
 
 @pytest.mark.parametrize("dims,levels,m", [((9, 7, 6), 2, 2), ((15, 17, 13), 3, 3), ((40, 36, 34), 3, 4),
-                                           ((128, 128, 128), 6, 16)],
+                                           ((44, 27, 21), 3, 3), ((72, 34, 66), 4, 4), ((128, 128, 128), 6, 16)],
                          ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
 def test_mixed_vcycle_matches_oracle(dims, levels, m):
     """The mixed form's V-cycle (float32 level 0, bfloat16 coarse levels) against the float64
