@@ -83,7 +83,8 @@ def test_restriction_is_full_weighting():
     assert multigrid.restrict(e, dims_f, dims_c)[:, 0].reshape(4, 4, 4)[1, 1, 1] == 1.0 / 16.0
 
 
-@pytest.mark.parametrize("dims,levels", [((7, 7, 7), 2), ((8, 6, 5), 2), ((8, 8, 8), 3), ((7, 9, 8), 3)])
+@pytest.mark.parametrize("dims,levels", [((7, 7, 7), 2), ((8, 6, 5), 2), ((8, 8, 8), 3), ((7, 9, 8), 3),
+                                         ((16, 14, 12), 4)])
 def test_vcycle_matches_dense_assembly(dims, levels):
     s = 2.0 + sum(dims)
     T = multigrid.VCycle(dims, s, levels)
