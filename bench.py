@@ -200,6 +200,31 @@ def replica_throughput(steps, world, t_ms):
     return world * steps / (t_ms / 1e3)
 
 
+def time_to_tol_over_seeds(solve, seeds, runs):
+    """Time to tol 1e-8 (solve only; setup reported apart) from the seeded starts `seeds`:
+    solve(seed) runs one solve and returns the solver's result dict.  Per seed one warm-up
+    solve, then the median of `runs` solves; the headline figures are the medians over the seeds
+    (the random start moves the iteration count by 10-20 %), the worst residual and status over
+    all of them.  Returns (the first timed result, the summary)."""
+    per_seed, first = [], None
+    for sd in seeds:
+        solve(sd)
+        rs = [solve(sd) for _ in range(runs)]
+        first = first or rs[0]
+        per_seed.append(dict(seed=sd, time_to_tol_s=statistics.median(r["solve_ms"] for r in rs) / 1e3,
+                             setup_s=statistics.median(r["setup_ms"] for r in rs) / 1e3,
+                             iters=rs[0]["iters"], fp64_sweeps=rs[0]["fp64_sweeps"], status=rs[0]["status_name"],
+                             max_rel_resid=max(r["max_rel_resid"] for r in rs)))
+    t = statistics.median(p["time_to_tol_s"] for p in per_seed)
+    iters = statistics.median(p["iters"] for p in per_seed)
+    bad = [p["status"] for p in per_seed if p["status"] != "ok"]
+    return first, dict(time_to_tol_s=t, setup_s=statistics.median(p["setup_s"] for p in per_seed),
+                       iters=iters, iters_per_s=iters / t, status=bad[0] if bad else "ok",
+                       max_rel_resid=max(p["max_rel_resid"] for p in per_seed),
+                       fp64_sweeps=max(p["fp64_sweeps"] for p in per_seed), tol=1e-8,
+                       seeds=[p["seed"] for p in per_seed], runs_per_seed=runs, per_seed=per_seed)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -274,28 +299,9 @@ def run_ours(args, rank, world, local_rank):
         return s, t_ms, launches, phase, clocks
 
     def time_to_tol(s):
-        """Time to tol 1e-8 (solve only; setup reported apart) from the seeded starts TTT_SEEDS
-        (offset by the rank): per seed one warm-up solve, then the median of TTT_RUNS solves; the
-        headline figures are the medians over the seeds (the random start moves the iteration
-        count by 10-20 %), the worst residual and status over all of them."""
-        per_seed, first = [], None
-        for sd in (x + len(TTT_SEEDS) * rank for x in TTT_SEEDS):
-            s.solve(m, tol=1e-8, maxit=300, seed=sd, with_vectors=False)
-            runs = [s.solve(m, tol=1e-8, maxit=300, seed=sd, with_vectors=False) for _ in range(TTT_RUNS)]
-            first = first or runs[0]
-            per_seed.append(dict(seed=sd, time_to_tol_s=statistics.median(r["solve_ms"] for r in runs) / 1e3,
-                                 setup_s=statistics.median(r["setup_ms"] for r in runs) / 1e3,
-                                 iters=runs[0]["iters"], fp64_sweeps=runs[0]["fp64_sweeps"],
-                                 status=runs[0]["status_name"],
-                                 max_rel_resid=max(r["max_rel_resid"] for r in runs)))
-        t = statistics.median(p["time_to_tol_s"] for p in per_seed)
-        iters = statistics.median(p["iters"] for p in per_seed)
-        bad = [p["status"] for p in per_seed if p["status"] != "ok"]
-        return first, dict(time_to_tol_s=t, setup_s=statistics.median(p["setup_s"] for p in per_seed),
-                           iters=iters, iters_per_s=iters / t, status=bad[0] if bad else "ok",
-                           max_rel_resid=max(p["max_rel_resid"] for p in per_seed),
-                           fp64_sweeps=max(p["fp64_sweeps"] for p in per_seed), tol=1e-8,
-                           seeds=[p["seed"] for p in per_seed], runs_per_seed=TTT_RUNS, per_seed=per_seed)
+        return time_to_tol_over_seeds(
+            lambda sd: s.solve(m, tol=1e-8, maxit=300, seed=sd, with_vectors=False),
+            [x + len(TTT_SEEDS) * rank for x in TTT_SEEDS], TTT_RUNS)
 
     # ---- float64 form: the timed steps of the JSON line
     sampler = ClockSampler(local_rank)

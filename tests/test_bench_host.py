@@ -1,0 +1,52 @@
+"""Host logic of bench.py's time-to-tol figure on CPU, with a fake solver: per seed one warm-up
+solve that is not timed, the median of the timed solves, the median over the seeds, and the worst
+status and residual over all of them."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class FakeSolves:
+    """solve(seed) -> a result dict; the first call for each seed (the warm-up) is an outlier."""
+
+    def __init__(self, ms, iters, status=None, resid=None):
+        self.ms, self.iters = ms, iters
+        self.status = status or {}
+        self.resid = resid or {}
+        self.calls = {}
+
+    def __call__(self, seed):
+        k = self.calls.get(seed, 0)
+        self.calls[seed] = k + 1
+        solve_ms = 1e9 if k == 0 else self.ms[seed][k - 1]
+        return dict(solve_ms=solve_ms, setup_ms=5.0, iters=self.iters[seed], fp64_sweeps=1,
+                    status_name=self.status.get(seed, "ok"), max_rel_resid=self.resid.get(seed, 1e-9),
+                    lam=[float(seed), float(k)])
+
+
+def test_medians_over_runs_then_seeds():
+    f = FakeSolves(ms={2: [100.0, 300.0, 200.0], 3: [90.0, 95.0, 400.0], 4: [500.0, 510.0, 505.0]},
+                   iters={2: 64, 3: 52, 4: 70})
+    first, d = bench.time_to_tol_over_seeds(f, [2, 3, 4], 3)
+    assert f.calls == {2: 4, 3: 4, 4: 4}                 # one warm-up + 3 timed per seed
+    per = {p["seed"]: p["time_to_tol_s"] for p in d["per_seed"]}
+    assert per == pytest.approx({2: 0.2, 3: 0.095, 4: 0.505})
+    assert d["time_to_tol_s"] == pytest.approx(0.2)      # median of 0.2, 0.095, 0.505
+    assert d["iters"] == 64 and d["iters_per_s"] == pytest.approx(64 / 0.2)
+    assert d["seeds"] == [2, 3, 4] and d["runs_per_seed"] == 3 and d["status"] == "ok"
+    assert first["lam"] == [2.0, 1.0]                    # the first timed solve of the first seed
+
+
+def test_worst_status_and_residual():
+    f = FakeSolves(ms={s: [10.0, 10.0] for s in (5, 6, 7)}, iters={5: 10, 6: 11, 7: 12},
+                   status={6: "not_converged"}, resid={7: 3e-7})
+    _, d = bench.time_to_tol_over_seeds(f, [5, 6, 7], 2)
+    assert d["status"] == "not_converged"
+    assert d["max_rel_resid"] == 3e-7
+    assert d["iters"] == 11
