@@ -72,3 +72,13 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert rc == capi.ERR_CUDA
     assert h.value is None
     assert capi.lobpcg_last_error(None) != ""
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the CUDA library the binding raises instead of falling back to anything else."""
+    monkeypatch.setattr(capi, "_lib", None)
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        capi.lib()
+    with pytest.raises(RuntimeError):
+        capi.lobpcg_destroy(None)
