@@ -170,3 +170,43 @@ def test_absolute_and_relative_tolerance_modes():
     assert np.all(rel.resid <= 1e-6 * rel.lam * (1 + 1e-6))
     assert np.all(ab.resid <= 1e-6 * (1 + 1e-6))
     assert ab.iters >= rel.iters     # lambda ~ 1e2 here, so the absolute test is stricter
+
+
+def test_exact_eigenspace_start_converges_at_pass_zero():
+    """X0 spanning the exact eigenspace of the m smallest eigenvalues: every residual is at the
+    rounding level at pass k = 0, so the loop exits there with iters = 0 and the closed-form
+    eigenvalues (the exit test of steps 7-8, reading R11)."""
+    dims = (5, 6, 7)                               # distinct axes: the smallest eigenvalues are simple
+    A = L.Laplace7(dims)
+    modes = laplace.exact_modes(dims, A.scale, 3)
+    X0 = np.stack([laplace.exact_eigenvector(dims, abc) for _, abc in modes], axis=1)
+    X0 = X0 @ np.array([[1.0, 0.3, -0.2], [0.0, 2.0, 0.5], [0.0, 0.0, 0.7]])   # any basis of the space
+    r = L.lobpcg(A, X0, 1e-8, 50, T=multigrid.VCycle(dims, A.scale, 2))
+    assert r.status == "converged" and r.iters == 0
+    want = np.array([lam for lam, _ in modes])
+    assert np.max(np.abs(r.lam - want) / want) < 1e-13
+
+
+def test_maxit_zero_only_checks_the_start():
+    dims = (6, 5, 4)
+    A = L.Laplace7(dims)
+    X0 = rng.uniform_block(2, A.n, 3)
+    r = L.lobpcg(A, X0, 1e-8, 0)
+    assert r.status == "not_converged" and r.iters == 0
+    # the result is the Rayleigh-Ritz of the start (steps 3-5): orthonormal X, Ritz values of span(X0)
+    assert np.max(np.abs(r.X.T @ r.X - np.eye(3))) < 1e-12
+    Q, _ = np.linalg.qr(X0)
+    H = Q.T @ A(Q)
+    assert np.max(np.abs(r.lam - np.linalg.eigvalsh(0.5 * (H + H.T))) / r.lam) < 1e-12
+
+
+@pytest.mark.parametrize("dims,m", [((7, 5, 3), 1), ((2, 1, 1), 1), ((2, 2, 1), 2), ((3, 2, 1), 3)])
+def test_single_vector_and_largest_block(dims, m):
+    """m = 1 (plain locally optimal preconditioned CG on one vector), tiny grids, and the largest
+    block m = n / 2: the m smallest eigenvalues of the dense operator."""
+    A = L.Laplace7(dims)
+    X0 = rng.uniform_block(3, A.n, m)
+    r = L.lobpcg(A, X0, 1e-10, 200, T=multigrid.VCycle(dims, A.scale, 1))
+    assert r.status == "converged"
+    want = np.linalg.eigvalsh(laplace.dense_matrix(dims, A.scale))[:m]
+    assert np.max(np.abs(r.lam - want) / want) < 1e-12
