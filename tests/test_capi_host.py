@@ -82,3 +82,44 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         capi.lib()
     with pytest.raises(RuntimeError):
         capi.lobpcg_destroy(None)
+
+
+def _default_args(argtypes):
+    out = []
+    for t in argtypes:
+        if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64):
+            out.append(0)
+        elif t is ctypes.c_double:
+            out.append(0.0)
+        else:
+            out.append(None)
+    return out
+
+
+def test_every_handle_call_rejects_a_null_handle(lib):
+    """Each entry point that takes a handle returns LOBPCG_ERR_ARG for a NULL one (host check, no
+    device work); destroy(NULL) is a no-op and last_error(NULL) returns the handle-free message."""
+    checked = []
+    for name, (res, argtypes) in capi._SIGNATURES.items():
+        if name in ("lobpcg_create", "lobpcg_gram_noalloc", "lobpcg_last_error", "lobpcg_destroy"):
+            continue
+        assert argtypes[0] is ctypes.c_void_p, name
+        rc = getattr(lib, name)(*_default_args(argtypes))
+        assert rc == capi.ERR_ARG, (name, rc)
+        checked.append(name)
+    assert len(checked) == len(capi._SIGNATURES) - 4
+    assert lib.lobpcg_destroy(None) == capi.OK
+
+
+def test_gram_noalloc_rejects_bad_arguments_before_device_work(lib):
+    f = lib.lobpcg_gram_noalloc
+    fake = ctypes.c_void_p(0x1000)                      # never dereferenced: the checks come first
+    # NULL inputs, n < 1, ld < n
+    assert f(None, None, None, None, None, None, 10, 10, 1, 0, 0, None, fake, None) == capi.ERR_ARG
+    assert f(fake, None, None, None, None, None, 0, 10, 1, 0, 0, None, fake, None) == capi.ERR_ARG
+    assert f(fake, None, None, None, None, None, 10, 9, 1, 0, 0, None, fake, None) == capi.ERR_ARG
+    # a second block without its pointer
+    assert f(fake, None, None, None, None, None, 10, 10, 1, 2, 0, None, fake, None) == capi.ERR_ARG
+    # basis wider than 96 columns
+    assert f(fake, fake, None, None, None, None, 1000, 1000, 60, 40, 0, None, fake, None) == capi.ERR_ARG
+    assert "96" in capi.lobpcg_last_error(None)
