@@ -184,6 +184,22 @@ def cpu_baseline_sample(w, iters=1):
     return 1.0 / per, per
 
 
+def cpu_single_thread_sample(w, iters=1):
+    """cpu_baseline_sample with one thread for every library call (BLAS, OpenMP): run in a child
+    process whose thread-count variables are set before numpy loads.  Returns (iters/s, s per
+    iteration), or None if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ("import json, bench; print(json.dumps(bench.cpu_baseline_sample(%r, %d)))" % (w, iters))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=1800)
+        ips, per = json.loads(r.stdout.strip().splitlines()[-1])
+        return float(ips), float(per)
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+
+
 def max_over_ranks(x, world, device):
     """The largest x over the ranks of the default process group (x itself when world = 1)."""
     import torch
@@ -234,6 +250,7 @@ def run_reference(args, rank, world):
     warm = 1
     ips, per = cpu_baseline_sample(w, iters=steps)
     cores = os.cpu_count()
+    single = cpu_single_thread_sample(w, iters=1) if w in ("c1", "c2") else None
     line = dict(impl="reference", metric=METRIC, value=ips, unit="iters/s", n_gpus=args.gpus, steps=steps,
                 warmup=warm, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
@@ -242,6 +259,9 @@ def run_reference(args, rank, world):
                                   sample=f"{steps} oracle LOBPCG iteration(s) of the same workload after its setup and pass 0 "
                                          "(numpy elementwise ops single-threaded, BLAS calls multi-threaded)"),
                 e2e=dict(value=ips, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    if single is not None:
+        line["cpu_baseline"]["single_thread"] = dict(value=single[0], unit="iters/s", cores=1,
+                                                     sample="1 oracle iteration, every library call on one thread")
     print(json.dumps(line), flush=True)
 
 

@@ -50,3 +50,12 @@ def test_worst_status_and_residual():
     assert d["status"] == "not_converged"
     assert d["max_rel_resid"] == 3e-7
     assert d["iters"] == 11
+
+
+def test_single_thread_oracle_sample_runs_in_a_child_process():
+    """The reference arm's one-thread oracle figure at the 48^3 workload: a child process with
+    every thread-count variable at 1 times one oracle iteration."""
+    out = bench.cpu_single_thread_sample("c1", iters=1)
+    assert out is not None
+    ips, per = out
+    assert ips > 0 and per > 0 and abs(ips * per - 1.0) < 1e-9
