@@ -14,7 +14,17 @@ W_J = W_J - Y (Y^T Y)^-1 (Y^T W_J); without Y both steps are empty.
 Readings of points the paper leaves open (each listed in the design notes):
 * convergence test (step 8): column j leaves J when ||A x_j - lambda_j x_j||_2
   <= tol * |lambda_j| (``tol_mode="relative"``, default) or <= tol
-  (``"absolute"``, the paper's literal wording); J only shrinks.
+  (``"absolute"``, the paper's literal wording); J only shrinks while columns
+  remain active.
+* final check (``final_check=True``, default): soft-locked columns stay in the
+  Rayleigh-Ritz basis (Section 2.3), and inside a cluster of equal Ritz values
+  the step-24 rotation can move part of an active column's error into a locked
+  one after its test.  So when J empties, every residual is recomputed from a
+  fresh A X (which also replaces the implicitly updated AX of steps 32-33);
+  columns above the tolerance re-enter J and the iteration continues; the solve
+  is converged only when this check passes, so every returned residual meets
+  the tolerance (the target the paper's tests state, Section 4.1).
+  ``final_check=False`` keeps the printed rule (exit as soon as J is empty).
 * loop bound (step 6, k = 0..MaxIterations): the pass k = maxit performs only
   steps 7-8; ``iters`` is the k at which J became empty.
 * Gram blocks (steps 18-22): the paper prints only the upper block triangle of
@@ -98,7 +108,8 @@ def _converged(norm, lam, tol, tol_mode):
     return norm <= bound
 
 
-def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False, on_pass=None, Y=None):
+def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", record=False, on_pass=None, Y=None,
+           final_check=True):
     """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity),
     in the complement of the constraint block Y ((n, l) array or None).
 
@@ -149,6 +160,15 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
                              orth=float(np.max(np.abs(X.T @ X - np.eye(m)))), dropped_p=False))
         J = [J[t] for t in keep]
         W = W[:, keep]
+        if not J and final_check:
+            # Final check: residuals of all m columns from a fresh A X; failing columns re-enter.
+            AX = A(X)
+            Rall = AX - X * lam[None, :]
+            norms_all = np.linalg.norm(Rall, axis=0)
+            J = [j for j in range(m) if not _converged(norms_all[j], lam[j], tol, tol_mode)]
+            W = Rall[:, J]
+            if record:
+                hist[-1]["recheck_J"] = list(J)
         if not J:
             status, iters = "converged", k
             break
