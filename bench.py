@@ -3,14 +3,15 @@
 
 A step is one LOBPCG iteration (Algorithm steps 7-33 of the BLOPEX paper, Section 2.2: residual,
 V-cycle preconditioner, Cholesky orthonormalisation of W and P, stencil SpMV, Gram matrices,
-Rayleigh-Ritz, Ritz update) over the whole block.  Default workload: the 7-point Dirichlet
-Laplacian on a 128^3 interior grid (2,097,152 unknowns), m = 16 eigenpairs, 6-level V-cycle.
-The JSON line's value is the float64 form; the mixed form (float32 / bfloat16 blocks, double-float
-X, float64 Rayleigh-Ritz and correction sweep) is timed the same way and reported beside it.  The
-timed steps run with tol = 0 so that every column stays active (fixed work per step); the time to
-reach tol = 1e-8 is measured separately for both forms.
+Rayleigh-Ritz, Ritz update) over the whole block.  Default workload: the paper's 10^8-unknown scale,
+the 7-point Dirichlet Laplacian on a 464^3 interior grid (99,897,344 unknowns), m = 8 eigenpairs,
+8-level V-cycle.  The JSON line's value is the float64 form; the mixed form (float32 / bfloat16
+blocks, double-float X, float64 Rayleigh-Ritz and correction sweep) is timed the same way and
+reported beside it.  The timed steps run with tol = 0 so that every column stays active (fixed work
+per step); the time to reach tol = 1e-8 is measured separately for both forms, with the
+per-eigenpair relative errors against the closed-form eigenvalues of the discrete Laplacian.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c4]
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU) every rank solves an
 independent replica with its own seed ("replicas only": the solver has no data-path collective);
@@ -38,10 +39,16 @@ WORKLOADS = {
     "c4": dict(dims=(464, 464, 464), m=8, levels=8),
 }
 
-# Time to tol: seeded starts, and timed solves per seed after one warm-up (medians over both);
-# fewer timed solves on the two largest grids.
+# Time to tol: seeded starts, and timed solves per seed after one warm-up solve (medians over
+# both); fewer timed solves on the two largest grids.
 TTT_SEEDS = (2, 3, 4)
 TTT_RUNS = {"c1": 5, "c2": 5, "c3": 3, "c4": 3}
+
+# The oracle's bounded sample for the CPU figures: one oracle iteration on a grid of the same m and
+# V-cycle whose point count the host finishes in seconds; the figure is scaled to the workload by
+# the ratio of point counts (every step of an iteration is O(n) at fixed m).
+CPU_SAMPLE = {"c1": "c1", "c2": "c2", "c3": "s3", "c4": "s4"}
+SAMPLES = {"s3": dict(dims=(96, 96, 96), m=32, levels=5), "s4": dict(dims=(128, 128, 128), m=8, levels=6)}
 
 # FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -60,6 +67,22 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 # DRAM traffic per launch of the Gram kernel (steps 17-23) from one ncu capture, keyed by the
 # SHA-256 of the kernel source it was taken on; a changed source invalidates it (traffic = null).
 NCU_TRAFFIC = {("c2", "b4503c8be547e48c"): 1.617388e9 + 13.800192e6}
+
+
+def closed_form_eigenvalues(dims, scale, m):
+    """The m smallest eigenvalues of the scaled 7-point Dirichlet Laplacian, scale * sum over the
+    axes of 4 sin^2(i pi / (2 (n + 1))) (the paper's Section 4.1 formula), ascending."""
+    import math
+    axes = [[4.0 * math.sin(i * math.pi / (2.0 * (n + 1))) ** 2 for i in range(1, min(n, m) + 1)] for n in dims]
+    vals = sorted(scale * (a + b + c) for a in axes[0] for b in axes[1] for c in axes[2])
+    return vals[:m]
+
+
+def rel_errors(lam, dims, m):
+    nx, ny, nz = dims
+    scale = float(nx + 1) ** 2 if nx == ny == nz else 1.0
+    exact = closed_form_eigenvalues(dims, scale, m)
+    return [abs(a - b) / abs(b) for a, b in zip(lam, exact)]
 
 
 def workload_desc(w):
@@ -170,10 +193,11 @@ def hbm_frac(nbytes, ms):
 
 
 def cpu_baseline_sample(w, iters=1):
-    """The oracle (numpy/scipy float64) timed on this host for `iters` iterations of workload w."""
+    """The oracle (numpy/scipy float64) timed on this host for `iters` iterations of workload (or
+    sample grid) w."""
     import numpy as np  # noqa: F401
     from oracle import lobpcg as olob, multigrid, rng
-    d = WORKLOADS[w]
+    d = WORKLOADS[w] if w in WORKLOADS else SAMPLES[w]
     A = olob.Laplace7(d["dims"])
     T = multigrid.VCycle(d["dims"], A.scale, d["levels"])
     X0 = rng.uniform_block(2, A.n, d["m"])
@@ -219,18 +243,18 @@ def replica_throughput(steps, world, t_ms):
 
 def time_to_tol_over_seeds(solve, seeds, runs):
     """Time to tol 1e-8 (solve only; setup reported apart) from the seeded starts `seeds`:
-    solve(seed) runs one solve and returns the solver's result dict.  Per seed one warm-up
-    solve, then the median of `runs` solves; the headline figures are the medians over the seeds
-    (the random start moves the iteration count by 10-20 %), the worst residual and status over
-    all of them.  Returns (the first timed result, the summary)."""
+    solve(seed) runs one solve and returns the solver's result dict.  One warm-up solve (first
+    seed), then per seed the median of `runs` solves; the headline figures are the medians over
+    the seeds (the random start moves the iteration count by 10-20 %), the worst residual and
+    status over all of them.  Returns (the first timed result, the summary)."""
     per_seed, first = [], None
+    solve(seeds[0])
     for sd in seeds:
-        solve(sd)
         rs = [solve(sd) for _ in range(runs)]
         first = first or rs[0]
         per_seed.append(dict(seed=sd, time_to_tol_s=statistics.median(r["solve_ms"] for r in rs) / 1e3,
                              setup_s=statistics.median(r["setup_ms"] for r in rs) / 1e3,
-                             iters=rs[0]["iters"], fp64_sweeps=rs[0]["fp64_sweeps"], status=rs[0]["status_name"],
+                             iters=rs[0]["iters"], fp64_checks=rs[0]["fp64_sweeps"], status=rs[0]["status_name"],
                              max_rel_resid=max(r["max_rel_resid"] for r in rs)))
     t = statistics.median(p["time_to_tol_s"] for p in per_seed)
     iters = statistics.median(p["iters"] for p in per_seed)
@@ -238,31 +262,57 @@ def time_to_tol_over_seeds(solve, seeds, runs):
     return first, dict(time_to_tol_s=t, setup_s=statistics.median(p["setup_s"] for p in per_seed),
                        iters=iters, iters_per_s=iters / t, status=bad[0] if bad else "ok",
                        max_rel_resid=max(p["max_rel_resid"] for p in per_seed),
-                       fp64_sweeps=max(p["fp64_sweeps"] for p in per_seed), tol=1e-8,
+                       fp64_checks=max(p["fp64_checks"] for p in per_seed), tol=1e-8,
                        seeds=[p["seed"] for p in per_seed], runs_per_seed=runs, per_seed=per_seed)
 
 
+def cpu_sample_desc(w):
+    """(sample key, its point count, scale factor to workload w, text)."""
+    key = CPU_SAMPLE[w]
+    d = WORKLOADS[key] if key in WORKLOADS else SAMPLES[key]
+    n_s = d["dims"][0] * d["dims"][1] * d["dims"][2]
+    wd = WORKLOADS[w]["dims"]
+    n_w = wd[0] * wd[1] * wd[2]
+    dims = "x".join(map(str, d["dims"]))
+    if n_s == n_w:
+        return key, n_s, 1.0, f"oracle LOBPCG iteration on the workload itself ({dims}, m={d['m']})"
+    return key, n_s, n_s / n_w, (f"oracle LOBPCG iteration on {dims}, m={d['m']}, {d['levels']} levels (same m), "
+                                 f"iters/s scaled to the workload by the point-count ratio {n_s}/{n_w}")
+
+
 def run_reference(args, rank, world):
+    """The oracle on the host cores: W warm-up steps and K timed steps, each step one oracle
+    iteration on the bounded sample grid of the workload (scaled to its iters/s)."""
     if rank != 0:
         return
+    import numpy as np  # noqa: F401
+    from oracle import lobpcg as olob, multigrid, rng
     w = args.workload
-    d = WORKLOADS[w]
-    steps = max(1, min(args.steps, 2))
-    warm = 1
-    ips, per = cpu_baseline_sample(w, iters=steps)
+    key, n_s, factor, text = cpu_sample_desc(w)
+    d = WORKLOADS[key] if key in WORKLOADS else SAMPLES[key]
+    A = olob.Laplace7(d["dims"])
+    T = multigrid.VCycle(d["dims"], A.scale, d["levels"])
+    X0 = rng.uniform_block(2, A.n, d["m"])
+    marks = []
+    # setup (steps 1-5) and pass 0 (no P block) are not steps; then W + K timed passes
+    olob.lobpcg(A, X0, 0.0, args.warmup + args.steps + 1, T=T, on_pass=lambda k: marks.append(time.perf_counter()))
+    timed = marks[args.warmup:]
+    per = (timed[-1] - timed[0]) / args.steps
+    ips = factor / per
     cores = os.cpu_count()
-    single = cpu_single_thread_sample(w, iters=1) if w in ("c1", "c2") else None
-    line = dict(impl="reference", metric=METRIC, value=ips, unit="iters/s", n_gpus=args.gpus, steps=steps,
-                warmup=warm, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+    single = cpu_single_thread_sample(key, iters=1) if w in ("c1", "c2", "c4") else None
+    wd = WORKLOADS[w]
+    line = dict(impl="reference", metric=METRIC, value=ips, unit="iters/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 / ips, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
-                config=dict(workload=workload_desc(w), grid=list(d["dims"]), m=d["m"], levels=d["levels"]),
+                config=dict(workload=workload_desc(w), grid=list(wd["dims"]), m=wd["m"], levels=wd["levels"]),
                 cpu_baseline=dict(value=ips, unit="iters/s", cores=cores, kind="oracle",
-                                  sample=f"{steps} oracle LOBPCG iteration(s) of the same workload after its setup and pass 0 "
-                                         "(numpy elementwise ops single-threaded, BLAS calls multi-threaded)"),
+                                  sample=f"each step one {text} (numpy elementwise ops single-threaded, "
+                                         "BLAS calls multi-threaded)"),
                 e2e=dict(value=ips, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     if single is not None:
-        line["cpu_baseline"]["single_thread"] = dict(value=single[0], unit="iters/s", cores=1,
-                                                     sample="1 oracle iteration, every library call on one thread")
+        line["cpu_baseline"]["single_thread"] = dict(value=single[0] * factor, unit="iters/s", cores=1,
+                                                     sample="1 " + text + ", every library call on one thread")
     print(json.dumps(line), flush=True)
 
 
@@ -350,51 +400,68 @@ def run_ours(args, rank, world, local_rank):
                h2d_bytes_per_step=n * m * 8 / args.steps, d2h_bytes_per_step=(n * m * 8 + m * 8) / args.steps,
                note="set_initial(pinned host X0) + solve(tol=0, maxit=K) + get_eigenpairs(to pinned host), wall clock")
     s64.close()
+    del X0, Xout
+    torch.cuda.empty_cache()
 
     # ---- mixed form (float32 / bfloat16 blocks, double-float X, float64 sweep)
     smx, tmx, launches_mx, phmx, _ = timed_form("mixed")
     outmx, tttmx = time_to_tol(smx)
     smx.close()
+    torch.cuda.empty_cache()
     lam_diff = max(abs(a - b) / abs(b) for a, b in zip(outmx["lam"], out64["lam"]))
 
-    # ---- per-kernel HBM rooflines from the phase events (all m columns active, b = m)
+    # ---- per-phase HBM fractions from the phase events (all m columns active, b = m)
     q = 3 * m
-    kern64 = dict(residual_step7=hbm_frac(3 * 8 * n * m, ph64["residual"]),
-                  spmv_step12=hbm_frac(2 * 8 * n * m, ph64["spmv"]),
-                  vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 8, 8), ph64["precond"]),
-                  gram_steps17_23=hbm_frac(2 * q * 8 * n, ph64["gram"]),
-                  note="float64 stencil and V-cycle are bound by GB300's float64 pipe (1/64 of float32), "
-                       "not by HBM")
-    kernmx = dict(residual_step7=hbm_frac(3 * 4 * n * m, phmx["residual"]),
-                  spmv_step12=hbm_frac(2 * 4 * n * m, phmx["spmv"]),
-                  vcycle_step9=hbm_frac(vcycle_bytes(dims, levels, m, 4, 2), phmx["precond"]),
-                  gram_steps17_23=hbm_frac((2 * q + 2 * m) * 4 * n, phmx["gram"]),
-                  update_steps25_33=hbm_frac((2 * m + 2 * m + 3 * m) * 4 * n, phmx["update"]))
+
+    def frac(nbytes, ms):
+        return round(hbm_frac(nbytes, ms)["frac"], 3)
+
+    kern64 = dict(residual=frac(3 * 8 * n * m, ph64["residual"]), spmv=frac(2 * 8 * n * m, ph64["spmv"]),
+                  vcycle=frac(vcycle_bytes(dims, levels, m, 8, 8), ph64["precond"]),
+                  gram=frac(2 * q * 8 * n, ph64["gram"]))
+    kernmx = dict(residual=frac(3 * 4 * n * m, phmx["residual"]), spmv=frac(2 * 4 * n * m, phmx["spmv"]),
+                  vcycle=frac(vcycle_bytes(dims, levels, m, 4, 2), phmx["precond"]),
+                  gram=frac((2 * q + 2 * m) * 4 * n, phmx["gram"]),
+                  update=frac((2 * m + 2 * m + 3 * m) * 4 * n, phmx["update"]))
 
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        ips, per = cpu_baseline_sample(w, iters=1)
-        cpu = dict(value=ips, unit="iters/s", cores=os.cpu_count(), kind="oracle",
-                   sample="1 oracle LOBPCG iteration of the same workload after its setup and pass 0 "
-                          "(numpy elementwise single-threaded, BLAS multi-threaded)")
+        key, _, factor, text = cpu_sample_desc(w)
+        ips, per = cpu_baseline_sample(key, iters=1)
+        cpu = dict(value=ips * factor, unit="iters/s", cores=os.cpu_count(), kind="oracle",
+                   sample="1 " + text + " (numpy elementwise single-threaded, BLAS multi-threaded)")
+
+    def rnd(x, k=4):
+        return float(f"{x:.{k}g}")
+
+    def ttt_brief(t, out):
+        return dict(time_to_tol_s=rnd(t["time_to_tol_s"]), iters=t["iters"], iters_per_s=rnd(t["iters_per_s"]),
+                    status=t["status"], max_rel_resid=rnd(t["max_rel_resid"], 3), fp64_checks=t["fp64_checks"],
+                    setup_s=rnd(t["setup_s"]),
+                    per_seed=[[p["seed"], rnd(p["time_to_tol_s"]), p["iters"]] for p in t["per_seed"]],
+                    rel_err_vs_closed_form=[rnd(e, 2) for e in rel_errors(out["lam"], dims, m)])
+
     line = dict(
         metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=t64 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f64", data="synthetic",
         config=dict(workload=workload_desc(w), grid=list(dims), m=m, levels=levels, tol_timed=0.0,
-                    l2="no flush: the 6 stored blocks are 1.6 GB, far above the 129 MB L2",
+                    l2=f"no flush: the 6 stored blocks are {6 * n * m * 8 / 1e9:.1f} GB, far above the 129 MB L2",
                     parallelism="replicas" if world > 1 else "single-gpu"),
-        time_to_tol=dict(fp64=ttt64, mixed=tttmx, mixed_speedup=ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"],
-                         max_rel_lambda_diff_mixed_vs_fp64=lam_diff),
-        mixed=dict(value=replica_throughput(args.steps, world, tmx), unit="iters/s", ms_per_step=tmx / args.steps,
-                   dtype="f64+f32+bf16", gpu_launches=launches_mx, phase_ms_per_iter=phmx, kernels_hbm=kernmx),
-        phase_ms_per_iter=ph64, kernels_hbm=kern64,
+        time_to_tol=dict(tol=1e-8, seeds=list(TTT_SEEDS), runs_per_seed=TTT_RUNS[w],
+                         fp64=ttt_brief(ttt64, out64), mixed=ttt_brief(tttmx, outmx),
+                         mixed_speedup=rnd(ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"], 3),
+                         max_rel_lambda_diff_mixed_vs_fp64=rnd(lam_diff, 2)),
         roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles, float64)", bound="alu",
                       achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=achieved / FP64_PEAK_TFLOPS,
                       traffic=traffic,
                       peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
+        mixed=dict(value=replica_throughput(args.steps, world, tmx), unit="iters/s", ms_per_step=tmx / args.steps,
+                   dtype="f64+f32+bf16", gpu_launches=launches_mx,
+                   phase_ms=dict((k, rnd(v)) for k, v in phmx.items()), hbm_frac=kernmx),
+        phase_ms=dict((k, rnd(v)) for k, v in ph64.items()), hbm_frac=kern64, hbm_peak_gbs=HBM_PEAK_GBS,
         hbm_peak_source=HBM_PEAK_SOURCE,
         cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
     print(json.dumps(line), flush=True)
@@ -463,7 +530,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner-pcg-sweep", default=None,
                     help="comma-separated inner PCG iteration counts: print that sweep instead of the bench line")

@@ -46,7 +46,9 @@ extern "C" {
 #define LOBPCG_ERR_BREAKDOWN  -4   /* Gram matrix of X or W_J not positive definite */
 #define LOBPCG_ERR_NONFINITE  -5   /* NaN or Inf in the iterates            */
 #define LOBPCG_ERR_STATE      -6   /* call out of order                     */
-#define LOBPCG_ERR_TIMEOUT    -7   /* reserved: no kernel of this library waits */
+#define LOBPCG_ERR_TIMEOUT    -7   /* a bounded wait inside a kernel (an mbarrier of a TMA
+                                      ring or of the tensor-core pipeline) gave up; the
+                                      kernel recorded it and returned, the handle stays usable */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define LOBPCG_FP64            0   /* every step in float64                 */
@@ -97,7 +99,9 @@ typedef struct lobpcg_info {
     int32_t iters;           /* iterations performed (k at which J became empty)  */
     int32_t active;          /* |J| at exit                                       */
     int32_t p_dropped;       /* iterations in which the P block was dropped       */
-    int32_t fp64_sweeps;     /* mixed form: float64 correction sweeps performed   */
+    int32_t fp64_sweeps;     /* float64 confirmations performed: mixed form, correction
+                                sweeps; float64 form, final checks (every residual from a
+                                fresh A X once J is empty)                         */
     int32_t reserved;
     double  max_rel_resid;   /* max_j ||A x_j - l_j x_j|| / |l_j|, from A X at exit */
     double  setup_ms;        /* device time of steps 1-5                           */
@@ -114,7 +118,8 @@ typedef struct lobpcg_info {
  * or LOBPCG_MIXED.  In the mixed form, once every implicit residual passes the
  * tolerance, a float64 correction sweep (steps 3-4 of the algorithm on the
  * current X with a float64 A X) recomputes the Ritz pairs and their residuals;
- * columns that still fail re-enter the iteration (at most 8 sweeps).
+ * columns that still fail re-enter the iteration (at most 16 sweeps; then the
+ * solve returns LOBPCG_NOT_CONVERGED).
  * On success *h receives the handle.  Errors: ERR_ARG, ERR_CUDA. */
 int lobpcg_create(lobpcg_t** h, int device, void* stream,
                   const lobpcg_allocator* alloc, int precision);
@@ -182,6 +187,19 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
 #define LOBPCG_ENGINE_TENSOR   2
 int lobpcg_set_gram_engine(lobpcg_t* h, int engine);
 
+/* Failure detection: the float32 kernels of the mixed form that stream their
+ * inputs through a ring of shared-memory stages filled by the Tensor Memory
+ * Accelerator (the SIMT Gram tiles and the streamed block products) wait for
+ * each stage on an mbarrier, and every such wait is bounded: after `polls`
+ * unsuccessful polls it gives up, the kernel waits (with its own, unchanged
+ * bound) for the copies it still has in flight, records the failure and
+ * returns, and the call returns LOBPCG_ERR_TIMEOUT with the handle still
+ * usable.  polls < 0 restores the default bound (2^22 polls, seconds); polls =
+ * 0 makes every such wait give up at once, which lets a caller exercise its
+ * handling of LOBPCG_ERR_TIMEOUT without a hung GPU.  The tensor-core Gram
+ * engine keeps its fixed bounds.  Never returns an error for a valid handle. */
+int lobpcg_set_wait_limit(lobpcg_t* h, int polls);
+
 /* Constraints, the hard locking of the paper's Section 2.3 (Section 2.2, steps 2
  * and 10): Y is an n-by-l block (column j at Y + j * ldy, float64, device memory,
  * or host memory if on_host != 0) of l linearly independent columns; it is
@@ -208,6 +226,12 @@ int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on
 
 /* Solve: steps 1-5, then iterations k = 0..maxit of steps 7-33 until every
  * column satisfies the tolerance (the pass k = maxit performs only steps 7-8).
+ * Soft-locked columns stay in the Rayleigh-Ritz basis (Section 2.3), so a
+ * locked column can drift above the tolerance; when J is empty the float64
+ * form therefore recomputes every residual from a fresh A X (which replaces
+ * the implicitly updated AX) and returns the failing columns to J, and the
+ * mixed form runs its float64 correction sweep.  The solve converges only when
+ * that check passes: on LOBPCG_OK every residual meets the tolerance.
  * Without lobpcg_set_initial, X0 is the seeded SplitMix64 block: entry
  * (p, j) = 2 * (out[p + n j] >> 11) * 2^-53 - 1, out = outputs of SplitMix64
  * started at state `seed`.  1 <= m <= LOBPCG_MAX_M, m <= n/2; tol >= 0;
@@ -364,7 +388,10 @@ int lobpcg_op_rayleigh_ritz(lobpcg_t* h, int q, int m, const double* gramA,
  * without waiting for it.  Limit: q = w0 + w1 + w2 <= 96, else LOBPCG_ERR_ARG.
  * No cudaMalloc, cudaFree or other allocating routine is called.  The first
  * call on a device looks up the array's device address and caches it; make that
- * first call before any stream capture.  Every call reuses the same array: calls
+ * first call before any stream capture.  The cached address belongs to the
+ * device's primary context and stays valid for that context's lifetime: a
+ * process that resets the device (cudaDeviceReset) must not call this entry
+ * point on that device afterwards.  Every call reuses the same array: calls
  * whose kernels may overlap on the GPU (unordered streams or threads) race and
  * give wrong results, so order them.  Errors: LOBPCG_ERR_ARG, LOBPCG_ERR_CUDA;
  * the message is returned by lobpcg_last_error(NULL) on the calling thread. */

@@ -49,6 +49,7 @@ _SIGNATURES = {
     "lobpcg_set_preconditioner": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double]),
     "lobpcg_set_options": (c_int, [c_void_p, c_int, c_int, c_int]),
     "lobpcg_set_gram_engine": (c_int, [c_void_p, c_int]),
+    "lobpcg_set_wait_limit": (c_int, [c_void_p, c_int]),
     "lobpcg_set_inner_pcg": (c_int, [c_void_p, c_int]),
     "lobpcg_set_initial": (c_int, [c_void_p, c_void_p, c_int, c_int64, c_int]),
     "lobpcg_set_constraints": (c_int, [c_void_p, c_void_p, c_int, c_int64, c_int]),
@@ -126,6 +127,10 @@ def lobpcg_set_options(h, tol_mode, gram_mode, phase_timing):
 
 def lobpcg_set_gram_engine(h, engine):
     return _call("lobpcg_set_gram_engine", h, engine)
+
+
+def lobpcg_set_wait_limit(h, polls):
+    return _call("lobpcg_set_wait_limit", h, polls)
 
 
 def lobpcg_set_inner_pcg(h, iters):

@@ -15,6 +15,9 @@
 namespace lg {
 
 extern std::atomic<long long> g_kernel_launches;
+// Poll limit of the stage waits of the TMA-staged float32 kernels for the calling thread's
+// current call (set from the handle for the duration of each call; < 0: the default).
+extern thread_local int g_wait_limit;
 
 struct Error : std::runtime_error {
     int code;
@@ -65,6 +68,7 @@ enum StatusBits : unsigned {
     ST_X_BREAKDOWN = 8u,      // chol(X^T X) failed (step 3)
     ST_NONFINITE = 16u,       // non-finite value in a small dense matrix
     ST_TIMEOUT = 32u,         // a bounded wait of a kernel gave up (its results are invalid)
+    ST_TIMEOUT_MMA = 64u,     // the tensor-core Gram's wait for its issued MMAs gave up as well
 };
 
 // Storage types of the blocks: float64 (FP64 form; X and AX of the mixed form), float32 (the

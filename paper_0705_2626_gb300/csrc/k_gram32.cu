@@ -50,6 +50,7 @@ struct G32Args {
     int K;                      // rows per stage
     int ks;                     // lanes per tile
     int nstage;                 // depth of the buffer ring
+    int spin;                   // polls a stage wait may take before it gives up
     int loff;                   // double-float tiles: staged offset of the lo plane
     int ntiles, tpc, ngroups;   // tiles, tiles per block, blocks per chunk
     int64_t rows_per_chunk, part_stride;
@@ -135,10 +136,10 @@ __global__ void __launch_bounds__(kG32Threads, DF ? 1 : 2)
 
     const int steps = a.K / (4 * a.ks);                       // float4 steps per lane and stage
     const int flush_every = max(1, (32 * a.ks) / a.K);        // >= 32 rows per float32 run
-    bool failed = false;
+    int failed_at = -1;
     for (int st = 0; st < nst; ++st) {
         const int buf = st % a.nstage;
-        const bool ok = mbar_wait(&full[buf], (unsigned)((st / a.nstage) & 1));
+        const bool ok = mbar_wait(&full[buf], (unsigned)((st / a.nstage) & 1), a.spin);
         if (ok && active) {
             const float* sm = stages + buf * stage_floats;
             for (int s = 0; s < steps; ++s) {
@@ -206,16 +207,21 @@ __global__ void __launch_bounds__(kG32Threads, DF ? 1 : 2)
             }
         }
         if (__syncthreads_or(!ok)) {
-            failed = true;
+            failed_at = st;
             break;
         }
         if (tid == 0 && st + a.nstage < nst) issue(st + a.nstage);
     }
-    if (failed) {
+    if (failed_at >= 0) {
         if (tid == 0) {
             atomicOr(status, ST_TIMEOUT);
-            // let the copies already issued land before the block exits (bounded as well)
-            for (int st = 0; st < nst; ++st) (void)mbar_wait(&full[st % a.nstage], (unsigned)((st / a.nstage) & 1));
+            // Stages before failed_at were consumed; those issued after it -- up to failed_at +
+            // nstage - 1 -- may still be in flight and must land before the block exits.  One
+            // budget of polls bounds the whole clean-up.
+            int budget = kSpinLimit;
+            const int issued_end = min(nst, failed_at + a.nstage);
+            for (int st = failed_at; st < issued_end; ++st)
+                (void)mbar_wait_budget(&full[st % a.nstage], (unsigned)((st / a.nstage) & 1), budget);
         }
         return;
     }
@@ -333,6 +339,7 @@ void g32_launch(G32Args& a, int64_t n, int64_t ld, const G32Block* blk, int nblk
     const int64_t stage_bytes = (int64_t)Q * a.K * sizeof(float);
     const int64_t budget = DF ? kG32SmemBudget : kG32SmemBudget / 2;    // two float32 blocks per SM
     a.nstage = (int)std::max<int64_t>(2, std::min<int64_t>(6, (budget - 2 * kG32Header) / stage_bytes));
+    a.spin = stage_wait_polls();
     LG_REQUIRE(2 * kG32Header + a.nstage * stage_bytes <= 227 * 1024, LOBPCG_ERR_ARG, "Gram stage too large");
     a.rows_per_chunk = ceil_div(ceil_div(n, nchunks), 128) * 128;
     // encode the column blocks (rows beyond n read as zeros)

@@ -336,9 +336,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ++u;
                 }
             }
-            // every MMA issued so far has completed once `fin` flips
+            // every MMA issued so far has completed once `fin` flips.  This wait ignores the abort
+            // flag: the accumulators are deallocated and the stage ring released only after the
+            // MMAs issued before an abort have finished (bounded; ST_TIMEOUT_MMA if even that
+            // wait gives up).
             mma_commit(fin);
-            if (!mbar_wait_or_abort(fin, 0u, abort_flag)) fail();
+            if (!mbar_wait(fin, 0u)) {
+                fail();
+                atomicOr(status, ST_TIMEOUT_MMA);
+            }
         }
     } else {
         const int wt = tid - 64;

@@ -37,6 +37,7 @@ struct TsmmArgs {
     int Q;                  // staged columns
     int TP;                 // points per tile
     int nstage;
+    int spin;               // polls a stage wait may take before it gives up
     int mode;
     int ncols;              // output columns
     int wl;                 // PROJECT: columns of [L0 L1];  UPDATE: m
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     const bool active = c0 < a.ncols;
     for (int it = 0; it < mine; ++it) {
         const int buf = it % a.nstage;
-        const bool ok = mbar_wait(&full[buf], (unsigned)((it / a.nstage) & 1));
+        const bool ok = mbar_wait(&full[buf], (unsigned)((it / a.nstage) & 1), a.spin);
         const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
         const int64_t p0 = tile * a.TP + 4 * pl;
         if (ok && active && p0 < a.n) {
@@ -243,8 +244,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(err, ST_TIMEOUT);
+                // the stages issued from `it` on may still be in flight; one budget of polls
+                int budget = kSpinLimit;
                 for (int j = it; j < min(mine, it + a.nstage); ++j)
-                    (void)mbar_wait(&full[j % a.nstage], (unsigned)((j / a.nstage) & 1));
+                    (void)mbar_wait_budget(&full[j % a.nstage], (unsigned)((j / a.nstage) & 1), budget);
             }
             return;
         }
@@ -276,6 +279,7 @@ void tsmm_launch(TsmmArgs& a, const TsBlock* blk, int nblk, const double* C, int
     a.cp = (a.ncols + 3) & ~3;
     const int64_t coef_bytes = (int64_t)crows * a.cp * 4;
     a.nstage = (int)std::max<int64_t>(2, std::min<int64_t>(4, (kSmemBudget - coef_bytes) / stage_bytes));
+    a.spin = stage_wait_polls();
     const size_t smem = 2 * kHeader + a.nstage * stage_bytes + coef_bytes;
     LG_REQUIRE(smem <= 227 * 1024, LOBPCG_ERR_ARG, "streamed product does not fit in shared memory");
     // tensor maps of the non-empty blocks, in the order of their staged offsets

@@ -29,6 +29,7 @@ using namespace lg;
 namespace lg {
 std::atomic<long long> g_kernel_launches{0};
 thread_local std::string g_handle_free_error;
+thread_local int g_wait_limit = -1;
 }  // namespace lg
 
 namespace {
@@ -77,6 +78,7 @@ struct lobpcg_handle {
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
     int gram_engine = LOBPCG_ENGINE_AUTO;       // float32 Grams of the mixed form
     int inner_pcg = 0;                          // inner PCG iterations of step 9 (0: V-cycle directly)
+    int wait_limit = -1;                        // poll limit of the TMA stage waits (< 0: default)
     Buf pcg_small;                              // inner PCG scalars: rz, rz', pAp (b each), active flags
 
     // workspace for a block of wm columns
@@ -117,6 +119,7 @@ struct lobpcg_handle {
     std::vector<double> norm_by_col;            // those norms, indexed by column
     int p_dropped = 0;
     int fp64_sweeps = 0;
+    int final_checks = 0;                       // float64 form: final checks performed
     double setup_ms = 0.0, solve_ms = 0.0;
     double phase_ms[LOBPCG_NPHASES] = {};
     cudaEvent_t ev[LOBPCG_NPHASES + 3] = {};   // phase marks, solve start / end, end of the residual
@@ -677,6 +680,7 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     h->k = 0;
     h->p_dropped = 0;
     h->fp64_sweeps = 0;
+    h->final_checks = 0;
     h->J.clear();
     std::fill(h->phase_ms, h->phase_ms + LOBPCG_NPHASES, 0.0);
     h->state = 0;
@@ -894,6 +898,25 @@ void fp64_correction(lobpcg_t* h) {
     h->pending_check = true;
 }
 
+// Float64 form, once J is empty: the final check.  Soft-locked columns stay in the Rayleigh-Ritz
+// basis (Section 2.3) and, inside a cluster of equal Ritz values, the step-24 rotation can lift a
+// locked column above the tolerance after its test.  So A X is recomputed (it replaces the
+// implicitly updated AX), the residuals of all m columns are tested, and the failing ones re-enter
+// J (check_and_lock compacts W to them).  The solve converges only when this check passes.
+void fp64_final_check(lobpcg_t* h) {
+    const int m = h->m;
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
+    h->J.resize(m);
+    for (int j = 0; j < m; ++j) h->J[j] = j;
+    residual_into_W(h);
+    const unsigned stw = fetch_small(h);
+    LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+    ++h->final_checks;
+    h->pending_check = true;
+}
+
 // Residuals of all m columns from A X (not the implicitly updated AX); host resid.
 void finish(lobpcg_t* h) {
     const int64_t n = h->g.n();
@@ -921,7 +944,7 @@ void fill_info(lobpcg_t* h, lobpcg_info* out, int status) {
     out->iters = h->k;
     out->active = (int)h->J.size();
     out->p_dropped = h->p_dropped;
-    out->fp64_sweeps = h->fp64_sweeps;
+    out->fp64_sweeps = h->precision == LOBPCG_MIXED ? h->fp64_sweeps : h->final_checks;
     double mr = 0.0;
     for (int j = 0; j < (int)h->resid_h.size() && j < (int)h->lam_h.size(); ++j)
         mr = std::max(mr, h->resid_h[j] / std::fabs(h->lam_h[j]));
@@ -943,6 +966,9 @@ int run_passes(lobpcg_t* h, int steps) {
             if (h->fp64_sweeps >= kMaxFp64Sweeps) break;   // not confirmed: NOT_CONVERGED
             fp64_correction(h);
             empty = check_and_lock(h);
+        } else if (empty) {
+            fp64_final_check(h);
+            empty = check_and_lock(h);
         }
         if (empty) { rc = LOBPCG_OK; break; }
         if (s == steps) break;
@@ -957,10 +983,17 @@ int run_passes(lobpcg_t* h, int steps) {
 }
 
 // ------------------------------------------------------------------ C-ABI plumbing
+// The handle's stage-wait limit for the duration of one call on the calling thread.
+struct WaitLimitScope {
+    explicit WaitLimitScope(int limit) { g_wait_limit = limit; }
+    ~WaitLimitScope() { g_wait_limit = -1; }
+};
+
 template <class F>
 int guarded(lobpcg_t* h, F&& f) {
     if (!h) return LOBPCG_ERR_ARG;
     if (h->poisoned) return LOBPCG_ERR_CUDA;
+    WaitLimitScope wait_scope(h->wait_limit);
     try {
         LG_CUDA(cudaSetDevice(h->device));
         h->err.clear();
@@ -1149,6 +1182,13 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters) {
         LG_REQUIRE(iters == 0 || h->precision == LOBPCG_FP64, LOBPCG_ERR_ARG,
                    "inner PCG needs a LOBPCG_FP64 handle");
         h->inner_pcg = iters;
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_set_wait_limit(lobpcg_t* h, int polls) {
+    return guarded(h, [&] {
+        h->wait_limit = polls < 0 ? -1 : polls;
         return LOBPCG_OK;
     });
 }

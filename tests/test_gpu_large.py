@@ -39,12 +39,9 @@ def test_paper_top_size_464(precision):
     assert out["status_name"] == "ok", out["status_name"]
     assert np.max(np.abs(lam - exact) / exact) < (1e-10 if precision == "fp64" else 1e-9)
     assert orth < 1e-12
-    if precision == "mixed":
-        assert out["max_rel_resid"] <= 1e-8 * (1 + 1e-6)     # confirmed by the float64 sweep
-    else:
-        # the float64 form updates AX implicitly (steps 25-33) and never re-checks soft-locked
-        # columns; the residual recomputed at exit is reported, and stays within a small multiple
-        assert out["max_rel_resid"] < 1e-6
+    # confirmed in float64: the mixed form's correction sweep, the float64 form's final check
+    assert out["max_rel_resid"] <= 1e-8 * (1 + 1e-6)
+    assert out["fp64_sweeps"] >= 1
 
 
 def test_mixed_256_m32():

@@ -4,7 +4,9 @@ lobpcg_gram_noalloc serves callers that may not allocate device memory (host cal
 applications whose pool owns all device memory, callers without a handle).  It keeps its
 partial sums in one fixed device array that every call reuses, so this test makes two calls in a
 row with different shapes and checks both against lobpcg_op_gram, with the tolerance of the Gram
-parity test.  The file name sorts last so that a run stopping at its first failure has already
+parity test, and checks that the device's free memory is the same before and after each call
+(after one first call, which loads the library's code onto the device and looks up the array's
+address).  The file name sorts last so that a run stopping at its first failure has already
 run every other test.
 """
 import ctypes
@@ -36,6 +38,13 @@ def test_noalloc_gram_matches_handle_gram_twice(dims):
     s = Solver(dims, precond="none")
     n = s.n
     stream = torch.cuda.current_stream().cuda_stream
+    # first call: module load and address lookup (not measured)
+    x = torch.ones((1, n), dtype=torch.float64, device="cuda")
+    g1 = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    assert capi.lobpcg_gram_noalloc(ptr(x), None, None, None, None, None, n, n, 1, 0, 0, None, ptr(g1),
+                                    ctypes.c_void_p(stream)) == capi.OK
+    torch.cuda.synchronize()
+    assert abs(g1.item() - n) <= 1e-12 * n
     for call, widths in enumerate([(8, 5, 5), (16, 16, 16)]):
         q = sum(widths)
         g = np.random.default_rng(100 + call)
@@ -51,8 +60,11 @@ def test_noalloc_gram_matches_handle_gram_twice(dims):
             if which == "handle":
                 rc = capi.lobpcg_op_gram(s.h, *args, ld, *widths, ptr(gA), ptr(gB))
             else:
+                torch.cuda.synchronize()
+                free_before = torch.cuda.mem_get_info()[0]
                 rc = capi.lobpcg_gram_noalloc(*args, n, ld, *widths, ptr(gA), ptr(gB), ctypes.c_void_p(stream))
-                torch.cuda.current_stream().synchronize()
+                torch.cuda.synchronize()
+                assert torch.cuda.mem_get_info()[0] == free_before      # nothing was allocated
             assert rc == capi.OK, capi.lobpcg_last_error(None)
             outs[which] = (gA.cpu().numpy().T, gB.cpu().numpy().T)
         nrmS, nrmA = np.linalg.norm(S, axis=0), np.linalg.norm(AS, axis=0)
