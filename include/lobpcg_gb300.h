@@ -68,7 +68,8 @@ extern "C" {
 #define LOBPCG_GRAM_EXPLICIT   0   /* all Gram blocks computed, symmetrised */
 #define LOBPCG_GRAM_PAPER      1   /* Lambda / I diagonal blocks (steps 18-22 as printed) */
 
-#define LOBPCG_MAX_M          32   /* largest block size m                  */
+#define LOBPCG_MAX_M         100   /* largest block size m (float64 form)   */
+#define LOBPCG_MAX_M_MIXED    32   /* largest block size m of the mixed form */
 #define LOBPCG_NPHASES         8
 
 /* Phase indices of lobpcg_info.phase_ms. */

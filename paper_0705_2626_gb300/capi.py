@@ -24,7 +24,8 @@ PRECOND_NONE, PRECOND_GMG = 0, 1
 TOL_RELATIVE, TOL_ABSOLUTE = 0, 1
 GRAM_EXPLICIT, GRAM_PAPER = 0, 1
 ENGINE_AUTO, ENGINE_SIMT, ENGINE_TENSOR = 0, 1, 2
-MAX_M = 32
+MAX_M = 100
+MAX_M_MIXED = 32
 NPHASES = 8
 PHASE_NAMES = ["residual", "precond", "cholqr_w", "spmv", "cholqr_p", "gram", "rayleigh_ritz", "update"]
 

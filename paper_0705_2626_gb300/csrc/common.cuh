@@ -46,6 +46,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 constexpr int kMaxM = LOBPCG_MAX_M;
 constexpr int kMaxQ = 3 * LOBPCG_MAX_M;   // Rayleigh-Ritz basis [X W_J P_J]
+constexpr int kMaxMMixed = LOBPCG_MAX_M_MIXED;
 constexpr int kNumSMs = 152;              // GB300: 2 dies x 76 SMs
 
 // Interior grid of one multigrid level; point p = i + nx*(j + ny*k).
@@ -134,7 +135,7 @@ struct Blocks3 {
 };
 // Gram partial sums over `nparts` row ranges: part has nparts * 2*q*q doubles; float64 blocks
 // and arithmetic (the float32 Grams of the mixed form are in k_gram32.cu).
-int gram_parts(int64_t n);
+int gram_parts(int64_t n, int q);
 int64_t gram_scratch_doubles(int64_t n, int q);
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st);

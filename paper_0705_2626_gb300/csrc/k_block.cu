@@ -113,12 +113,22 @@ __host__ __device__ inline int block_of(const Blocks3& B, int c) {
 
 // Output tile (ti, tj) of S^T AS is needed when it holds an entry (i, j) with
 // block(i) <= block(j): the upper block triangle of steps 18 / 21, diagonal blocks in full.
-__host__ __device__ inline bool a_tile_needed(const Blocks3& B, int q, int ti, int tj) {
-    return block_of(B, ti * kTM) <= block_of(B, min(tj * kTM + kTM - 1, q - 1));
+// First tile column of the needed A tiles in tile row ti: the tile holding the first column of
+// the block of column ti * kTM (block(j) >= block(i) from there on).
+__host__ __device__ inline int a_tile_first(const Blocks3& B, int ti) {
+    const int b = block_of(B, ti * kTM);
+    const int c0 = b == 0 ? 0 : (b == 1 ? B.w[0] : B.w[0] + B.w[1]);
+    return c0 / kTM;
 }
 
+constexpr int kGramMaxThreads = 768;            // threads of one Gram block
+constexpr int kGramSmemMax = 200 * 1024;        // stage buffers and group reduction
+constexpr int kGramSmemPair = 96 * 1024;        // narrow bases: two blocks per SM
+
 struct GramShape {
-    int ntA, ntB, ks, gk;    // needed A tiles, upper B tiles, row groups, rows per stage
+    int ntA, ntB, nt;   // needed A tiles, upper B tiles, all tiles
+    int tpb, ngroups;   // tiles per thread block, thread blocks (tile groups) per row range
+    int ks, gk;         // row groups per tile, rows per stage
 };
 
 __host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a, int elt) {
@@ -127,26 +137,36 @@ __host__ __device__ inline GramShape gram_shape(const Blocks3& S, bool with_a, i
     GramShape g;
     g.ntA = 0;
     if (with_a)
-        for (int ti = 0; ti < T; ++ti)
-            for (int tj = 0; tj < T; ++tj) g.ntA += a_tile_needed(S, q, ti, tj);
+        for (int ti = 0; ti < T; ++ti) g.ntA += T - a_tile_first(S, ti);
     g.ntB = T * (T + 1) / 2;
-    const int nt = g.ntA + g.ntB;
-    g.ks = max(1, min(8, 256 / nt));     // narrow bases: several row groups per tile
-    // keep the stage buffers and the group reduction within 48 KB of shared memory
-    while (g.ks > 1 && max(2 * 16 * g.ks * (T * kTM + 1) * elt, g.ks * nt * 16 * 8) > 48 * 1024) --g.ks;
+    g.nt = g.ntA + g.ntB;
+    // wide bases: the tiles are split over ngroups thread blocks that share a row range
+    g.ngroups = (g.nt + kGramMaxThreads - 1) / kGramMaxThreads;
+    g.tpb = (g.nt + g.ngroups - 1) / g.ngroups;
+    // narrow bases: several row groups per tile, about 256 threads, and at most 96 KB of shared
+    // memory so that two blocks share an SM (one stages its rows while the other computes)
+    g.ks = max(1, min(64, 256 / g.tpb));
+    const int arrays = with_a ? 2 : 1;
+    while (g.ks > 1 && max(arrays * 16 * g.ks * (T * kTM + 1) * elt, g.ks * g.tpb * 16 * 8) > kGramSmemPair) --g.ks;
     g.gk = 16 * g.ks;
     return g;
 }
 
+__host__ __device__ inline size_t gram_smem_bytes(const GramShape& g, int q, bool with_a, int elt) {
+    const int T = (q + kTM - 1) / kTM;
+    const size_t stage = (size_t)(with_a ? 2 : 1) * g.gk * (T * kTM + 1) * elt;
+    const size_t red = g.ks > 1 ? (size_t)g.ks * g.tpb * 16 * sizeof(double) : 0;
+    return stage > red ? stage : red;
+}
+
 // Partial sums over one row range per thread block of the needed tiles of S^T AS ("A") and of
-// the upper tiles of S^T S ("B").  Thread t works on tile t % nt for the rows of each
-// shared-memory stage congruent to t / nt modulo ks (16 rows per stage and thread); the ks
-// row groups are added in a fixed order at the end.  Tiles are numbered row-major, so a warp
-// shares ti (broadcast reads of S).  C = double: float64 products and sums.  C = float:
+// the upper tiles of S^T S ("B").  Tiles are numbered A first, then B, each row-major; thread
+// block (r, y) takes the tiles y * tpb .. y * tpb + tpb - 1 of row range r.  Thread t works on
+// its block's tile t % tpb for the rows of each shared-memory stage congruent to t / tpb modulo
+// ks (16 rows per stage and thread); the ks row groups are added in a fixed order at the end.
+// A warp shares ti (broadcast reads of S).  C = double: float64 products and sums.  C = float:
 // float32 products summed over the 16 rows of a stage, stage sums added with Kahan's
 // compensated summation, the result rounded to float64.
-constexpr int kGramMaxThreads = 768;   // q <= 96: at most 684 tiles of 4 x 4
-
 template <typename T0, typename T12, typename C>
 __global__ void __launch_bounds__(kGramMaxThreads)
     k_gram(int64_t n, int64_t rows_per_part, Blocks3 S, Blocks3 AS, int with_a,
@@ -156,25 +176,24 @@ __global__ void __launch_bounds__(kGramMaxThreads)
     const int q = S.q();
     const int T = (q + kTM - 1) / kTM;
     const GramShape gs = gram_shape(S, with_a != 0, (int)sizeof(C));
-    const int nt = gs.ntA + gs.ntB;
+    const int tpb = gs.tpb;
     const int ldsm = T * kTM + 1;                 // odd row length: conflict-free stores
     C* sS = sm;                                   // [gk][ldsm]
     C* sA = sm + gs.gk * ldsm;                    // [gk][ldsm]
-    const int tile = threadIdx.x % nt;
-    const int grp = threadIdx.x / nt;
-    const bool active = grp < gs.ks;
+    const int tl = threadIdx.x % tpb;
+    const int grp = threadIdx.x / tpb;
+    const int tile = blockIdx.y * tpb + tl;
+    const bool active = grp < gs.ks && tile < gs.nt;
     const bool isA = tile < gs.ntA;
     int ti = 0, tj = 0;
     if (isA) {
         int u = tile;                             // u-th needed A tile, row-major
-        for (int a = 0; a < T * T; ++a) {
-            const int ai = a / T, aj = a % T;
-            if (a_tile_needed(S, q, ai, aj)) {
-                if (u == 0) { ti = ai; tj = aj; break; }
-                --u;
-            }
+        for (int r = 0; r < T; ++r) {
+            const int first = a_tile_first(S, r), cnt = T - first;
+            if (u < cnt) { ti = r; tj = first + u; break; }
+            u -= cnt;
         }
-    } else {
+    } else if (tile < gs.nt) {
         int u = tile - gs.ntA;                    // upper B tiles ti <= tj, row-major
         while (u >= T - ti) { u -= T - ti; ++ti; }
         tj = ti + u;
@@ -190,17 +209,30 @@ __global__ void __launch_bounds__(kGramMaxThreads)
     const int64_t r0 = blockIdx.x * rows_per_part;
     const int64_t r1 = min(n, r0 + rows_per_part);
     const C* rhs = isA ? sA : sS;
+    constexpr int kLoadBatch = 4;                 // loads in flight per thread while staging
+    const int nstage_elems = gs.gk * T * kTM;
     for (int64_t base = r0; base < r1; base += gs.gk) {
-        for (int e = threadIdx.x; e < gs.gk * T * kTM; e += blockDim.x) {
-            const int c = e / gs.gk, k = e - c * gs.gk;
-            const int64_t p = base + k;
-            C vs = 0, va = 0;
-            if (c < q && p < r1) {
-                vs = load_col<T0, T12, C>(S, c, p);
-                if (with_a) va = load_col<T0, T12, C>(AS, c, p);
+        for (int arr = 0; arr < (with_a ? 2 : 1); ++arr) {
+            const Blocks3& B = arr ? AS : S;
+            C* dst = arr ? sA : sS;
+            for (int e0 = threadIdx.x; e0 < nstage_elems; e0 += kLoadBatch * blockDim.x) {
+                C v[kLoadBatch];
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    const int c = e / gs.gk, k = e - c * gs.gk;
+                    const int64_t p = base + k;
+                    v[u] = (e < nstage_elems && c < q && p < r1) ? load_col<T0, T12, C>(B, c, p) : C(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < nstage_elems) {
+                        const int c = e / gs.gk, k = e - c * gs.gk;
+                        dst[k * ldsm + c] = v[u];
+                    }
+                }
             }
-            sS[k * ldsm + c] = vs;
-            if (with_a) sA[k * ldsm + c] = va;
         }
         __syncthreads();
         if (active) {
@@ -242,25 +274,25 @@ __global__ void __launch_bounds__(kGramMaxThreads)
         }
     // add the row groups in order 0, 1, ..., ks-1 (the stage buffers are free now)
     if (gs.ks > 1) {
-        double* red = reinterpret_cast<double*>(sm_raw);   // [ks][nt][16]
+        double* red = reinterpret_cast<double*>(sm_raw);   // [ks][tpb][16]
         if (active)
 #pragma unroll
             for (int u = 0; u < kTM; ++u)
 #pragma unroll
-                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * nt + tile) * 16 + u * kTM + v] = res[u][v];
+                for (int v = 0; v < kTM; ++v) red[((int64_t)grp * tpb + tl) * 16 + u * kTM + v] = res[u][v];
         __syncthreads();
-        if (grp == 0) {
+        if (grp == 0 && active) {
 #pragma unroll
             for (int u = 0; u < kTM; ++u)
 #pragma unroll
                 for (int v = 0; v < kTM; ++v) {
-                    double sum = red[(int64_t)tile * 16 + u * kTM + v];
-                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * nt + tile) * 16 + u * kTM + v];
+                    double sum = red[(int64_t)tl * 16 + u * kTM + v];
+                    for (int g = 1; g < gs.ks; ++g) sum += red[((int64_t)g * tpb + tl) * 16 + u * kTM + v];
                     res[u][v] = sum;
                 }
         }
     }
-    if (grp != 0) return;
+    if (grp != 0 || !active) return;
     double* out = part + (int64_t)blockIdx.x * 2 * q * q + (isA ? 0 : (int64_t)q * q);
 #pragma unroll
     for (int u = 0; u < kTM; ++u)
@@ -357,19 +389,25 @@ __global__ void k_gram_finalize(int q, int nparts, const double* __restrict__ pa
 
 // Pout = S1 C1 + S2 C2 (arithmetic CW, stored TW) and Xout = S0 C0 + Pout (float64).
 // S0 is float64; S1, S2 have type TW.  Each thread owns one grid point and kCG output columns.
-template <typename TW, typename CW>
+// CG (float64 blocks only): the coefficients are read from C itself (wide bases whose q x m copy
+// would not fit in shared memory); all lanes of a warp read the same entry.
+template <typename TW, typename CW, bool CG>
 __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__ C,
                          double* Xout, TW* Pout, float* Xh, float* Xl, int64_t ldout,
                          const unsigned* __restrict__ status, unsigned skip) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    double* sC = reinterpret_cast<double*>(sm_raw);             // q x m, column-major
     const int q = S.q();
-    CW* sCw = reinterpret_cast<CW*>(sm_raw + sizeof(double) * q * m);   // copy in CW
     if (status && (*status & skip)) return;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < q * m; e += 32 * blockDim.y) {
-        sC[e] = C[e];
-        sCw[e] = (CW)C[e];
+    double* cc = reinterpret_cast<double*>(sm_raw);                  // q x m, column-major
+    CW* cw = reinterpret_cast<CW*>(sm_raw + sizeof(double) * q * m);  // copy in CW
+    if constexpr (!CG) {
+        for (int e = threadIdx.y * 32 + threadIdx.x; e < q * m; e += 32 * blockDim.y) {
+            cc[e] = C[e];
+            cw[e] = (CW)C[e];
+        }
     }
+    const double* sC = CG ? C : cc;
+    const CW* sCw = CG ? reinterpret_cast<const CW*>(C) : cw;
     __syncthreads();
     const int c0 = threadIdx.y * kCG;
     const int w0 = S.w[0], w1 = S.w[1], w2 = S.w[2];
@@ -426,15 +464,18 @@ __global__ void k_update(int64_t n, int m, Blocks3 S, const double* __restrict__
 
 // V <- V Rinv with Rinv upper triangular (b x b, column-major): each thread owns one grid point
 // and kCG output columns c0..c0+kCG-1, so it needs input columns 0..c0+kCG-1 only.
-template <typename T>
+// RG (float64 only): Rinv is read from global memory (wide blocks).
+template <typename T, bool RG>
 __global__ void k_apply_upper(int64_t n, int b, const T* Vin, int64_t ldin, T* Vout, int64_t ldout,
                               const double* __restrict__ Rinv, const unsigned* __restrict__ status,
                               unsigned skip) {
     using C = typename Acc<T>::type;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    C* sR = reinterpret_cast<C*>(sm_raw);
     if (status && (*status & skip)) return;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < b * b; e += 32 * blockDim.y) sR[e] = (C)Rinv[e];
+    C* r = reinterpret_cast<C*>(sm_raw);
+    if constexpr (!RG)
+        for (int e = threadIdx.y * 32 + threadIdx.x; e < b * b; e += 32 * blockDim.y) r[e] = (C)Rinv[e];
+    const C* sR = RG ? reinterpret_cast<const C*>(Rinv) : r;
     __syncthreads();
     const int c0 = threadIdx.y * kCG;
     const int iend = min(b, c0 + kCG);
@@ -497,28 +538,39 @@ void launch_norms_finalize(int ncols, int nchunks, const double* partial, double
     LG_CHECK_LAUNCH();
 }
 
-int gram_parts(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 1024), 4 * kNumSMs));
+// Row ranges of the Gram partial sums: about 1024 rows each, at most 4 per SM, and for wide
+// bases at most as many as keep the partial sums (2 q^2 doubles per range) near 256 MB.
+int gram_parts(int64_t n, int q) {
+    const int64_t cap = std::max<int64_t>(kNumSMs, ((int64_t)1 << 25) / (2 * (int64_t)q * q));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ceil_div(n, 1024), 4 * kNumSMs), cap));
 }
 
-int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n) * 2 * q * q; }
+int64_t gram_scratch_doubles(int64_t n, int q) { return (int64_t)gram_parts(n, q) * 2 * q * q; }
 
 template <typename T0, typename T12, typename C>
 static void gram_t(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                    cudaStream_t st) {
     const int q = S.q();
-    const int T = (q + kTM - 1) / kTM;
+    LG_REQUIRE(q <= kMaxQ, LOBPCG_ERR_ARG, "Gram basis too wide");
     const GramShape gs = gram_shape(S, AS != nullptr, (int)sizeof(C));
-    const int nt = gs.ntA + gs.ntB;
-    const int threads = (int)ceil_div((int64_t)nt * gs.ks, 32) * 32;
+    const int threads = (int)ceil_div((int64_t)gs.tpb * gs.ks, 32) * 32;
     LG_REQUIRE(threads <= kGramMaxThreads, LOBPCG_ERR_ARG, "Gram basis too wide");
-    const size_t stage = 2 * (size_t)gs.gk * (T * kTM + 1) * sizeof(C);
-    const size_t red = gs.ks > 1 ? (size_t)gs.ks * nt * 16 * sizeof(double) : 0;
-    const size_t smem = std::max(stage, red);
-    LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "Gram shared memory too large");
+    const size_t smem = gram_smem_bytes(gs, q, AS != nullptr, (int)sizeof(C));
+    LG_REQUIRE(smem <= (size_t)kGramSmemMax, LOBPCG_ERR_ARG, "Gram shared memory too large");
+    if (smem > 48 * 1024) {
+        static bool attr[64] = {};
+        int dev = 0;
+        LG_CUDA(cudaGetDevice(&dev));
+        if (dev < 64 && !attr[dev]) {
+            LG_CUDA(cudaFuncSetAttribute((const void*)k_gram<T0, T12, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSmemMax));
+            attr[dev] = true;
+        }
+    }
     const int64_t rows = ceil_div(n, nparts);
     Blocks3 A = AS ? *AS : S;
-    k_gram<T0, T12, C><<<nparts, threads, smem, st>>>(n, rows, S, A, AS ? 1 : 0, part);
+    k_gram<T0, T12, C><<<dim3((unsigned)nparts, (unsigned)gs.ngroups), threads, smem, st>>>(n, rows, S, A,
+                                                                                           AS ? 1 : 0, part);
 }
 
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
@@ -550,12 +602,17 @@ void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void*
     if (b <= 0) return;
     const int groups = (int)ceil_div(b, kCG);
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 32), (int64_t)kNumSMs * 16);
-    if (t == DT_F32)
-        k_apply_upper<float><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(float), st>>>(
+    if (t == DT_F32) {
+        LG_REQUIRE((size_t)b * b * sizeof(float) <= 48 * 1024, LOBPCG_ERR_ARG, "float32 block too wide");
+        k_apply_upper<float, false><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(float), st>>>(
             n, b, (const float*)Vin, ldin, (float*)Vout, ldout, Rinv, status, skip_mask);
-    else
-        k_apply_upper<double><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(double), st>>>(
+    } else if ((size_t)b * b * sizeof(double) > 48 * 1024) {
+        k_apply_upper<double, true><<<(unsigned)blocks, dim3(32, groups), 0, st>>>(
             n, b, (const double*)Vin, ldin, (double*)Vout, ldout, Rinv, status, skip_mask);
+    } else {
+        k_apply_upper<double, false><<<(unsigned)blocks, dim3(32, groups), (size_t)b * b * sizeof(double), st>>>(
+            n, b, (const double*)Vin, ldin, (double*)Vout, ldout, Rinv, status, skip_mask);
+    }
     LG_CHECK_LAUNCH();
 }
 
@@ -567,12 +624,17 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
     const bool f32 = (S.w[1] + S.w[2] > 0 ? S.t12 : DT_F64) == DT_F32;
     if (f32) {
         const size_t smem = (size_t)S.q() * m * (sizeof(double) + sizeof(float));
-        k_update<float, float><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
+        LG_REQUIRE(smem <= 48 * 1024, LOBPCG_ERR_ARG, "float32 update too wide");
+        k_update<float, float, false><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
             n, m, S, C, Xout, (float*)Pout, Xh, Xl, ldout, status, skip_mask);
     } else {
         const size_t smem = (size_t)S.q() * m * (2 * sizeof(double));
-        k_update<double, double><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
-            n, m, S, C, Xout, (double*)Pout, Xh, Xl, ldout, status, skip_mask);
+        if (smem > 48 * 1024)
+            k_update<double, double, true><<<(unsigned)blocks, dim3(32, groups), 0, st>>>(
+                n, m, S, C, Xout, (double*)Pout, Xh, Xl, ldout, status, skip_mask);
+        else
+            k_update<double, double, false><<<(unsigned)blocks, dim3(32, groups), smem, st>>>(
+                n, m, S, C, Xout, (double*)Pout, Xh, Xl, ldout, status, skip_mask);
     }
     LG_CHECK_LAUNCH();
 }

@@ -11,29 +11,31 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;   // 2^-52
 
+constexpr int kRowsPerLane = (kMaxM + 31) / 32;
+
 // Lower-triangular inverse, column by column: warp w owns columns w, w + nwarps, ...; lane l
-// owns rows l, l + 32, l + 64 of the column.  L and Linv are row-major with leading dim ldl.
+// owns rows l, l + 32, l + 64, ... of the column.  L and Linv are row-major with leading dim ldl.
 __device__ void lower_inverse(int nq, const double* L, int ldl, double* Linv, int ldi) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = wid; j < nq; j += nw) {
-        double x[3];
+        double x[kRowsPerLane];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = (lane + 32 * r == j) ? 1.0 : 0.0;
+        for (int r = 0; r < kRowsPerLane; ++r) x[r] = (lane + 32 * r == j) ? 1.0 : 0.0;
         for (int k = j; k < nq; ++k) {
             const int ok = k & 31, rk = k >> 5;
             double xk = 0.0;
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < kRowsPerLane; ++r)
                 if (r == rk && lane == ok) { x[r] = x[r] / L[k * ldl + k]; xk = x[r]; }
             xk = __shfl_sync(0xffffffffu, xk, ok);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
+            for (int r = 0; r < kRowsPerLane; ++r) {
                 const int i = lane + 32 * r;
                 if (i > k && i < nq) x[r] = fma(-L[i * ldl + k], xk, x[r]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < kRowsPerLane; ++r) {
             const int i = lane + 32 * r;
             if (i < nq) Linv[i * ldi + j] = (i >= j) ? x[r] : 0.0;
         }
@@ -64,14 +66,16 @@ __device__ bool cholesky_lower(int nq, double* S, int lds, int* flag) {
     return true;
 }
 
+// S and its inverse Li (b x (b + 1) each, row-major) in dynamic shared memory.
 __global__ void k_chol_rinv(int b, const double* __restrict__ G, double* __restrict__ Rinv,
                             unsigned* status, unsigned fail_bit, unsigned skip) {
-    __shared__ double S[kMaxM * (kMaxM + 1)];
-    __shared__ double Li[kMaxM * (kMaxM + 1)];
+    extern __shared__ double smd[];
     __shared__ double d[kMaxM];
     __shared__ int flag;
     if (status && (*status & skip)) return;
-    const int ld = kMaxM + 1;
+    const int ld = b + 1;
+    double* S = smd;
+    double* Li = smd + b * ld;
     if (threadIdx.x == 0) flag = 0;
     __syncthreads();
     for (int e = threadIdx.x; e < b * b; e += blockDim.x)
@@ -112,7 +116,16 @@ __global__ void k_chol_rinv(int b, const double* __restrict__ G, double* __restr
 void launch_chol_rinv(int b, const double* G, double* Rinv, unsigned* status, unsigned fail_bit,
                       unsigned skip_mask, cudaStream_t st) {
     LG_REQUIRE(b >= 1 && b <= kMaxM, LOBPCG_ERR_ARG, "block width out of range");
-    k_chol_rinv<<<1, 256, 0, st>>>(b, G, Rinv, status, fail_bit, skip_mask);
+    const size_t smem = 2 * (size_t)b * (b + 1) * sizeof(double);
+    static bool attr[64] = {};
+    int dev = 0;
+    LG_CUDA(cudaGetDevice(&dev));
+    if (smem > 48 * 1024 && dev < 64 && !attr[dev]) {
+        LG_CUDA(cudaFuncSetAttribute((const void*)k_chol_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * (size_t)kMaxM * (kMaxM + 1) * sizeof(double))));
+        attr[dev] = true;
+    }
+    k_chol_rinv<<<1, 256, smem, st>>>(b, G, Rinv, status, fail_bit, skip_mask);
     LG_CHECK_LAUNCH();
 }
 

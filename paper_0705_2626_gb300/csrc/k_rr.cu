@@ -16,7 +16,10 @@
 //      then one orthonormalisation step V <- V (I + (I - V^T V) / 2);
 //   5. one block:  S = V^T M V is diagonal up to rounding except inside near-degenerate clusters;
 //                  float64 cyclic Jacobi sweeps that rotate only the pairs above 8 eps ||S||_F
-//                  finish it, then C = D Linv^T V Q for the m smallest, ascending.
+//                  finish it (rotations Q), eigenvalue order;
+//   6. m blocks:   C = D Linv^T V Q for the m smallest, ascending, one column per block.
+// The single-block kernels keep their matrices in shared memory while they fit (q up to about
+// 100 in float64, 158 in float32) and in the global work area beyond that (q up to 300).
 // Breakdown rule as elsewhere: a pivot of the unit-diagonal matrix at or below order * 2^-52.
 #include <algorithm>
 
@@ -27,16 +30,40 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 constexpr int kSubMax = 48;    // largest cleanup submatrix kept beside S and Q in shared memory
+constexpr size_t kRRSmemMax = 200 * 1024;   // dynamic shared memory of the single-block kernels
+constexpr int kRowsPerLane = (kMaxQ + 31) / 32;
 
-// work layout (doubles), all q x q matrices column-major with leading dimension q
+// work layout (doubles), all q x q matrices column-major with leading dimension q, except the
+// row-major scratch copies noted at their kernels
 struct RRWork {
-    double *Linv, *M, *V, *V2, *MV, *S, *R, *E, *d, *hdr;   // hdr[0] = nq, hdr[1] = ||M||_F
+    double *Linv, *M, *V, *V2, *MV, *S, *R, *E, *d, *hdr, *perm;   // hdr[0] = nq, hdr[1] = ||M||_F
     __host__ __device__ RRWork(double* w, int q) {
         const size_t q2 = (size_t)q * q;
         Linv = w; M = w + q2; V = w + 2 * q2; V2 = w + 3 * q2; MV = w + 4 * q2; S = w + 5 * q2;
-        R = w + 6 * q2; E = w + 7 * q2; d = w + 8 * q2; hdr = d + q;
+        R = w + 6 * q2; E = w + 7 * q2; d = w + 8 * q2; hdr = d + q; perm = hdr + 8;
     }
 };
+
+// Shared memory of the single-block kernels for basis width q (0: the work area is used).
+__host__ __device__ inline size_t rr_chol_smem(int q) {
+    const size_t b = 2 * (size_t)q * (q + 1) * sizeof(double);
+    return b <= kRRSmemMax ? b : 0;
+}
+__host__ __device__ inline size_t rr_jacobi_smem(int q) {
+    const size_t b = 2 * (size_t)q * (q + 1) * sizeof(float);
+    return b <= kRRSmemMax ? b : 0;
+}
+__host__ __device__ inline size_t rr_final_sub_bytes(int q) {
+    const int s = q < kSubMax ? q : kSubMax;
+    return 2 * (size_t)s * (s + 1) * sizeof(double);
+}
+__host__ __device__ inline bool rr_final_in_smem(int q) {
+    return 2 * (size_t)q * (q + 1) * sizeof(double) + rr_final_sub_bytes(q) <= kRRSmemMax;
+}
+__host__ __device__ inline size_t rr_final_smem(int q) {
+    return rr_final_in_smem(q) ? 2 * (size_t)q * (q + 1) * sizeof(double) + rr_final_sub_bytes(q)
+                               : rr_final_sub_bytes(q);
+}
 
 __device__ __forceinline__ int nq_of(const RRWork& w) { return (int)w.hdr[0]; }
 
@@ -68,31 +95,31 @@ __device__ bool chol_lower_rm(int nq, double* S, int lds, int* flag, double* rin
     return true;
 }
 
-// Linv (row-major in smem) by column-parallel forward substitution: warp w owns columns
-// w, w + nwarps, ...; lane l owns rows l, l + 32, l + 64.
+// Linv (row-major) by column-parallel forward substitution: warp w owns columns w, w + nwarps,
+// ...; lane l owns rows l, l + 32, l + 64, ...
 __device__ void lower_inv(int nq, const double* L, int ldl, double* Li, int ldi, double* dinv) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = threadIdx.x; k < nq; k += blockDim.x) dinv[k] = 1.0 / L[k * ldl + k];
     __syncthreads();
     for (int j = wid; j < nq; j += nw) {
-        double x[3];
+        double x[kRowsPerLane];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = (lane + 32 * r == j) ? 1.0 : 0.0;
+        for (int r = 0; r < kRowsPerLane; ++r) x[r] = (lane + 32 * r == j) ? 1.0 : 0.0;
         for (int k = j; k < nq; ++k) {
             const int ok = k & 31, rk = k >> 5;
             double xk = 0.0;
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < kRowsPerLane; ++r)
                 if (r == rk && lane == ok) { x[r] = x[r] * dinv[k]; xk = x[r]; }
             xk = __shfl_sync(0xffffffffu, xk, ok);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
+            for (int r = 0; r < kRowsPerLane; ++r) {
                 const int i = lane + 32 * r;
                 if (i > k && i < nq) x[r] = fma(-L[i * ldl + k], xk, x[r]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < kRowsPerLane; ++r) {
             const int i = lane + 32 * r;
             if (i < nq) Li[i * ldi + j] = (i >= j) ? x[r] : 0.0;
         }
@@ -107,9 +134,12 @@ __global__ void __launch_bounds__(1024)
     __shared__ double rinv, dinv[kMaxQ];
     if (*status & skip) return;
     RRWork w(work, q);
-    const int ld = q + 1;
-    double* Lsm = sm;                 // q x (q+1), row-major
-    double* Lism = sm + q * ld;       // q x (q+1), row-major
+    // L and its inverse, row-major: in shared memory (leading dimension q + 1) while they fit,
+    // else in the work area's R and E (leading dimension q; both are free until step 4)
+    const bool in_smem = rr_chol_smem(q) != 0;
+    const int ld = in_smem ? q + 1 : q;
+    double* Lsm = in_smem ? sm : w.R;
+    double* Lism = in_smem ? sm + q * ld : w.E;
     int nq = (*status & ST_P_DROPPED) ? q_min : q;
     const int tid = threadIdx.x;
     for (;;) {
@@ -290,9 +320,12 @@ __global__ void __launch_bounds__(1024)
     if (*status & skip) return;
     RRWork w(work, q);
     const int nq = nq_of(w);
-    const int ld = nq + 1;
-    float* A = smf;
-    float* V = smf + nq * ld;
+    // A and V in shared memory while they fit, else (float32, leading dimension nq) in the work
+    // area's MV, which is free until step 4
+    const bool in_smem = rr_jacobi_smem(q) != 0;
+    const int ld = in_smem ? nq + 1 : nq;
+    float* A = in_smem ? smf : reinterpret_cast<float*>(w.MV);
+    float* V = A + nq * ld;
     for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
         const int i = e / nq, j = e % nq;
         A[i * ld + j] = (float)(0.5 * (w.M[i + (int64_t)q * j] + w.M[j + (int64_t)q * i]));
@@ -402,19 +435,24 @@ __global__ void __launch_bounds__(256) k_rr_oa_e(int q, double* work, const unsi
     }
 }
 
-// ---------------------------------------------------------------- 5. cleanup and output
+// ---------------------------------------------------------------- 5. cleanup
+// S symmetrised (A) and the cleanup rotations Q: in shared memory (row-major, leading dimension
+// nq + 1) while they fit, else in the work area's R and E (row-major, leading dimension q).
+// Writes Q row-major into E (leading dimension q), the order of the eigenvalues into perm and the
+// m smallest eigenvalues into lam.
 __global__ void __launch_bounds__(1024)
-    k_rr_final(int q, int m, double* work, double* __restrict__ lam, double* __restrict__ C,
-               unsigned* status, unsigned skip) {
+    k_rr_final(int q, int m, double* work, double* __restrict__ lam, unsigned* status, unsigned skip) {
     extern __shared__ double sm[];
     __shared__ double rc[kMaxQ / 2 + 1], rs[kMaxQ / 2 + 1], red[32], lsort[kMaxQ];
-    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], perm[kMaxQ], rotated, act[kMaxQ], idx[kMaxQ], nact;
+    __shared__ int rp[kMaxQ / 2 + 1], rr[kMaxQ / 2 + 1], rotated, act[kMaxQ], idx[kMaxQ], nact;
     if (*status & skip) return;
     RRWork w(work, q);
     const int nq = nq_of(w);
-    const int ld = nq + 1;
-    double* A = sm;             // S, symmetrised, row-major
-    double* Q = sm + nq * ld;   // accumulated cleanup rotations
+    const bool in_smem = rr_final_in_smem(q);
+    const int ld = in_smem ? nq + 1 : q;
+    double* A = in_smem ? sm : w.R;               // S, symmetrised, row-major
+    double* Q = in_smem ? sm + nq * ld : w.E;     // accumulated cleanup rotations, row-major
+    double* sub = in_smem ? Q + nq * ld : sm;     // the cleanup submatrix and its rotations
     for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
         const int i = e / nq, j = e % nq;
         A[i * ld + j] = 0.5 * (w.S[i + (int64_t)q * j] + w.S[j + (int64_t)q * i]);
@@ -446,7 +484,7 @@ __global__ void __launch_bounds__(1024)
         jacobi_sweeps<double>(nq, A, ld, Q, ld, thr, 16, rc, rs, rp, rr, &rotated);
     } else if (na >= 2) {
         const int lds = na + 1;
-        double* As = Q + nq * ld;          // na x na submatrix and its rotations
+        double* As = sub;                  // na x na submatrix and its rotations
         double* Qs = As + na * lds;
         for (int e = threadIdx.x; e < na * na; e += blockDim.x) {
             const int a = e / na, b = e % na;
@@ -470,26 +508,41 @@ __global__ void __launch_bounds__(1024)
             const double lj = A[j * ld + j];
             rank += (lj < li) || (lj == li && j < i);
         }
-        perm[rank] = i;
+        w.perm[rank] = (double)i;
         lsort[rank] = li;
         if (!isfinite(li)) atomicOr(status, (unsigned)ST_NONFINITE);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < m; r += blockDim.x) lam[r] = lsort[r];
-    // Y[:, r] = V2 Q[:, perm r] (reuse MV as Y), then C = D Linv^T Y
-    for (int e = threadIdx.x; e < nq * m; e += blockDim.x) {
-        const int i = e % nq, r = e / nq;
-        const int pc = perm[r];
+    if (in_smem)
+        for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
+            const int i = e / nq, j = e % nq;
+            w.E[i * (int64_t)q + j] = Q[i * ld + j];
+        }
+}
+
+// ---------------------------------------------------------------- 6. output, one column per block
+// y = V2 Q[:, perm r] (V2 the refined eigenvectors of M), then C[:, r] = D Linv^T y.
+__global__ void __launch_bounds__(256)
+    k_rr_out(int q, double* work, double* __restrict__ C, const unsigned* status, unsigned skip) {
+    __shared__ double qc[kMaxQ], y[kMaxQ];
+    if (*status & skip) return;
+    RRWork w(work, q);
+    const int nq = nq_of(w);
+    const int r = blockIdx.x;
+    const int pc = (int)w.perm[r];
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) qc[k] = w.E[k * (int64_t)q + pc];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
         double s = 0.0;
-        for (int k = 0; k < nq; ++k) s = fma(w.V2[i + (int64_t)q * k], Q[k * ld + pc], s);
-        w.MV[i + (int64_t)q * r] = s;
+        for (int k = 0; k < nq; ++k) s = fma(w.V2[i + (int64_t)q * k], qc[k], s);
+        y[i] = s;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < q * m; e += blockDim.x) {
-        const int i = e % q, r = e / q;
+    for (int i = threadIdx.x; i < q; i += blockDim.x) {
         double s = 0.0;
         if (i < nq) {
-            for (int k = i; k < nq; ++k) s = fma(w.Linv[k + (int64_t)q * i], w.MV[k + (int64_t)q * r], s);
+            for (int k = i; k < nq; ++k) s = fma(w.Linv[k + (int64_t)q * i], y[k], s);
             s *= w.d[i];
         }
         C[i + (int64_t)q * r] = s;
@@ -504,7 +557,7 @@ void set_smem(const void* f, size_t bytes) {
 
 }  // namespace
 
-int64_t rr_work_doubles(int q) { return 8 * (int64_t)q * q + 2 * q + 8; }
+int64_t rr_work_doubles(int q) { return 8 * (int64_t)q * q + 3 * q + 8; }
 
 void launch_rayleigh_ritz(int q, int q_min, int m, const double* gramA, const double* gramB,
                           double* lam, double* C, double* work, unsigned* status,
@@ -515,22 +568,18 @@ void launch_rayleigh_ritz(int q, int q_min, int m, const double* gramA, const do
     static bool attr[64] = {};
     int dev = 0;
     LG_CUDA(cudaGetDevice(&dev));
-    const size_t big64 = 2 * (size_t)kMaxQ * (kMaxQ + 1) * sizeof(double);
-    const size_t fin64 = big64 + 2 * (size_t)kSubMax * (kSubMax + 1) * sizeof(double);
     if (dev < 64 && !attr[dev]) {
-        set_smem((const void*)k_rr_chol, big64);
-        set_smem((const void*)k_rr_final, fin64);
-        set_smem((const void*)k_rr_jacobi32, 2 * (size_t)kMaxQ * (kMaxQ + 1) * sizeof(float));
+        set_smem((const void*)k_rr_chol, kRRSmemMax);
+        set_smem((const void*)k_rr_final, kRRSmemMax);
+        set_smem((const void*)k_rr_jacobi32, kRRSmemMax);
         attr[dev] = true;
     }
-    const size_t s64 = 2 * (size_t)q * (q + 1) * sizeof(double);
-    const size_t s32 = 2 * (size_t)q * (q + 1) * sizeof(float);
     const unsigned skip = skip_mask | ST_RR_BREAKDOWN;
-    k_rr_chol<<<1, 1024, s64, st>>>(q, q_min, gramB == nullptr ? 1 : 0, gramB, work, status, skip_mask);
+    k_rr_chol<<<1, 1024, rr_chol_smem(q), st>>>(q, q_min, gramB == nullptr ? 1 : 0, gramB, work, status, skip_mask);
     LG_CHECK_LAUNCH();
     k_rr_form_m<<<q, 128, 0, st>>>(q, gramA, work, status, skip);
     LG_CHECK_LAUNCH();
-    k_rr_jacobi32<<<1, 1024, s32, st>>>(q, work, status, skip);
+    k_rr_jacobi32<<<1, 1024, rr_jacobi_smem(q), st>>>(q, work, status, skip);
     LG_CHECK_LAUNCH();
     for (int it = 0; it < 2; ++it) {
         k_rr_gemm<<<q, 128, 0, st>>>(q, 0, work, status, skip);   // MV = M V
@@ -557,8 +606,9 @@ void launch_rayleigh_ritz(int q, int q_min, int m, const double* gramA, const do
     LG_CHECK_LAUNCH();
     k_rr_gemm<<<q, 128, 0, st>>>(q, 2, work, status, skip);       // S = V^T M V
     LG_CHECK_LAUNCH();
-    const size_t sfin = s64 + 2 * (size_t)std::min(q, kSubMax) * (std::min(q, kSubMax) + 1) * sizeof(double);
-    k_rr_final<<<1, 1024, sfin, st>>>(q, m, work, lam, C, status, skip);
+    k_rr_final<<<1, 1024, rr_final_smem(q), st>>>(q, m, work, lam, status, skip);
+    LG_CHECK_LAUNCH();
+    k_rr_out<<<m, 256, 0, st>>>(q, work, C, status, skip);
     LG_CHECK_LAUNCH();
 }
 

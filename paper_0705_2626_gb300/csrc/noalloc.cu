@@ -34,6 +34,7 @@ extern thread_local std::string g_handle_free_error;
 namespace {
 
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;   // 8 MiB
+constexpr int kNoAllocMaxQ = 96;                                 // widest basis q
 constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code `g_gram_scratch` is a host-side stand-in, not a device
@@ -84,7 +85,7 @@ extern "C" int lobpcg_gram_noalloc(const double* S0, const double* S1, const dou
         err = "lobpcg_gram_noalloc: invalid arguments";
         return LOBPCG_ERR_ARG;
     }
-    if (q > 3 * LOBPCG_MAX_M || (size_t)2 * q * q > kNoAllocScratchDoubles) {
+    if (q > kNoAllocMaxQ || (size_t)2 * q * q > kNoAllocScratchDoubles) {
         err = "lobpcg_gram_noalloc: basis width q = " + std::to_string(q) +
               " exceeds the maximum of 96 columns";
         return LOBPCG_ERR_ARG;
@@ -93,7 +94,7 @@ extern "C" int lobpcg_gram_noalloc(const double* S0, const double* S1, const dou
     const int rc = scratch_address(&scratch, err);
     if (rc != LOBPCG_OK) return rc;
     const int nparts = (int)std::max<int64_t>(
-        1, std::min<int64_t>(gram_parts(n), (int64_t)(kNoAllocScratchDoubles / (2 * (size_t)q * q))));
+        1, std::min<int64_t>(gram_parts(n, q), (int64_t)(kNoAllocScratchDoubles / (2 * (size_t)q * q))));
     try {
         Blocks3 S{};
         S.p[0] = S0; S.w[0] = w0;

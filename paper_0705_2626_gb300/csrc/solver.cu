@@ -187,6 +187,8 @@ void free_varcoef(lobpcg_t* h) {
 // Workspace for blocks of up to wm columns (6m vectors of the algorithm + V-cycle buffers).
 void ensure_workspace(lobpcg_t* h, int wm) {
     if (h->wm >= wm && h->X.p) return;
+    LG_REQUIRE(h->precision == LOBPCG_FP64 || wm <= LOBPCG_MAX_M_MIXED, LOBPCG_ERR_ARG,
+               "block wider than the mixed form's limit of 32 columns");
     free_workspace(h);
     h->state = 0;   // a finished or running solve does not survive a reallocation
     const int64_t n = h->g.n();
@@ -211,8 +213,11 @@ void ensure_workspace(lobpcg_t* h, int wm) {
         ensure(h, h->lt[l], bytes);
     }
     const int q = 3 * wm;
+    // the float32 Gram kernels (mixed form and its kernel-level entry points) serve blocks of at
+    // most 32 columns
+    const int64_t g32 = wm <= LOBPCG_MAX_M_MIXED ? (int64_t)g32_chunks(n) * 2 * q * q : 0;
     h->part_doubles = (size_t)std::max<int64_t>(
-        std::max<int64_t>(gram_scratch_doubles(n, q), (int64_t)g32_chunks(n) * 2 * q * q),
+        std::max<int64_t>(gram_scratch_doubles(n, q), g32),
         std::max<int64_t>(residual_chunks(n), resid_mx_blocks(h->g)) * wm);
     ensure(h, h->part, h->part_doubles * sizeof(double));
     const size_t nsmall = 2 * (size_t)q * q + (size_t)q * wm + wm + (size_t)wm * wm + wm +
@@ -418,8 +423,8 @@ void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* 
           const double* paper_lam) {
     const int64_t n = h->g.n();
     const int q = S.q();
-    const int nparts = gram_parts(n);
-    LG_REQUIRE((size_t)nparts * 2 * q * q <= h->part_doubles, LOBPCG_ERR_ARG, "Gram scratch too small");
+    const int nparts = (int)std::min<int64_t>(gram_parts(n, q), (int64_t)(h->part_doubles / (2 * (size_t)q * q)));
+    LG_REQUIRE(nparts >= 1, LOBPCG_ERR_ARG, "Gram scratch too small");
     launch_gram(n, S, AS, f64(h->part), nparts, h->stream);
     launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
 }
@@ -668,7 +673,9 @@ void check_setup_status(lobpcg_t* h, unsigned stw) {
 void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     require_op(h);
     const int64_t n = h->g.n();
-    LG_REQUIRE(m >= 1 && m <= LOBPCG_MAX_M, LOBPCG_ERR_ARG, "m out of range [1, 32]");
+    LG_REQUIRE(m >= 1 && m <= LOBPCG_MAX_M, LOBPCG_ERR_ARG, "m out of range [1, 100]");
+    LG_REQUIRE(h->precision == LOBPCG_FP64 || m <= LOBPCG_MAX_M_MIXED, LOBPCG_ERR_ARG,
+               "m out of range [1, 32] for the mixed form");
     LG_REQUIRE(2 * (int64_t)m <= n, LOBPCG_ERR_ARG, "m too large for the grid (need m <= n/2)");
     LG_REQUIRE(2 * ((int64_t)m + h->ncon) <= n, LOBPCG_ERR_ARG,
                "m plus the constraint columns too large for the grid (need m + l <= n/2)");
@@ -1469,7 +1476,7 @@ int lobpcg_op_gram_f32(lobpcg_t* h, const float* S0, int w0, const float* S1, in
     return guarded(h, [&] {
         require_op(h);
         const int64_t n = h->g.n();
-        LG_REQUIRE(V && b >= 1 && b <= LOBPCG_MAX_M && w0 >= 0 && w1 >= 0 && w0 + w1 <= 2 * LOBPCG_MAX_M &&
+        LG_REQUIRE(V && b >= 1 && b <= LOBPCG_MAX_M_MIXED && w0 >= 0 && w1 >= 0 && w0 + w1 <= 2 * LOBPCG_MAX_M_MIXED &&
                        (w0 == 0 || S0) && (w1 == 0 || S1) && valid_ld(ld, n),
                    LOBPCG_ERR_ARG, "invalid float32 Gram arguments");
         ensure_workspace(h, std::max(h->wm, (w0 + w1 + b + 2) / 3));
@@ -1491,8 +1498,9 @@ int lobpcg_op_gram_residual(lobpcg_t* h, const float* Xh, const float* Xl, const
     return guarded(h, [&] {
         require_op(h);
         const int64_t n = h->g.n();
-        LG_REQUIRE(Xh && Xl && R && lambda && gramA && gramB && m >= 1 && m <= LOBPCG_MAX_M && b >= 1 &&
-                       b <= LOBPCG_MAX_M && bp >= 0 && bp <= LOBPCG_MAX_M && W && AW && (bp == 0 || (P && AP)) &&
+        LG_REQUIRE(Xh && Xl && R && lambda && gramA && gramB && m >= 1 && m <= LOBPCG_MAX_M_MIXED && b >= 1 &&
+                       b <= LOBPCG_MAX_M_MIXED && bp >= 0 && bp <= LOBPCG_MAX_M_MIXED && W && AW &&
+                       (bp == 0 || (P && AP)) &&
                        valid_ld(ld, n),
                    LOBPCG_ERR_ARG, "invalid residual-form Gram arguments");
         ensure_workspace(h, std::max(h->wm, (m + b + bp + 2) / 3));

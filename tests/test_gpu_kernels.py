@@ -160,7 +160,9 @@ def test_residual_and_norms(dims, m, cols):
 
 @pytest.mark.parametrize("dims,widths", [((33, 33, 33), (8, 5, 5)), ((10, 9, 8), (3, 0, 0)),
                                          ((16, 16, 16), (4, 4, 0)), ((128, 128, 128), (16, 16, 16)),
-                                         ((20, 20, 20), (32, 32, 32)), ((2, 3, 5), (7, 1, 2))])
+                                         ((20, 20, 20), (32, 32, 32)), ((2, 3, 5), (7, 1, 2)),
+                                         ((20, 19, 18), (50, 50, 50)), ((12, 12, 12), (100, 100, 100)),
+                                         ((64, 64, 64), (8, 0, 0))])
 def test_gram_matches_definition(dims, widths):
     s = make(dims, precond="none")
     n = s.n
@@ -207,7 +209,8 @@ def test_gram_is_deterministic():
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
-@pytest.mark.parametrize("dims,b", [((20, 20, 20), 6), ((9, 9, 9), 1), ((32, 32, 32), 32), ((128, 128, 128), 16)])
+@pytest.mark.parametrize("dims,b", [((20, 20, 20), 6), ((9, 9, 9), 1), ((32, 32, 32), 32), ((128, 128, 128), 16),
+                                   ((24, 24, 24), 100), ((40, 40, 40), 50)])
 def test_cholqr_matches_oracle(dims, b):
     s = make(dims, precond="none")
     n = s.n
@@ -248,7 +251,8 @@ def _sym_pair(q, seed, cluster=False):
 
 
 @pytest.mark.parametrize("q,m,cluster", [(24, 8, False), (48, 16, False), (96, 32, False), (48, 16, True),
-                                         (5, 5, False), (1, 1, False)])
+                                         (5, 5, False), (1, 1, False), (120, 40, False), (150, 50, True),
+                                         (240, 80, False), (300, 100, True)])
 def test_rayleigh_ritz_matches_oracle(q, m, cluster):
     s = make((4, 4, 4), precond="none")
     A, B = _sym_pair(q, q + m, cluster)

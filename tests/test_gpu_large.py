@@ -53,6 +53,27 @@ def test_mixed_256_m32():
     assert orth < 1e-12
 
 
+@pytest.mark.parametrize("dims", [(200, 200, 200), (200, 201, 202)], ids=["200cube", "200x201x202"])
+def test_paper_section_41_fifty_eigenpairs_one_block(dims):
+    """Section 4.1's accuracy test as the paper ran it: one block of m = 50 at tol 1e-6 (float64
+    form, Rayleigh-Ritz basis of 150 columns); every eigenvalue within 1e-8 relative of the closed
+    form, residuals at tol, orthonormal eigenvectors."""
+    s = Solver(dims, precision="fp64")
+    out = s.solve(50, tol=1e-6, maxit=500, seed=2)
+    X = out["X"]
+    G = X @ X.T
+    orth = float((G - torch.eye(50, dtype=G.dtype, device=G.device)).abs().max())
+    s.close()
+    del X, G
+    torch.cuda.empty_cache()
+    assert out["status_name"] == "ok", out["status_name"]
+    lam = np.array(out["lam"])
+    exact = laplace.exact_eigenvalues(dims, laplace.default_scale(dims), 50)
+    assert np.max(np.abs(lam - exact) / exact) < 1e-8
+    assert out["max_rel_resid"] <= 1e-6 * (1 + 1e-6)
+    assert orth < 1e-12
+
+
 @pytest.mark.parametrize("dims,precision", [((200, 200, 200), "mixed"), ((200, 201, 202), "mixed"),
                                             ((200, 201, 202), "fp64")],
                          ids=["200cube-mixed", "200x201x202-mixed", "200x201x202-fp64"])

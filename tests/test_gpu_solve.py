@@ -188,7 +188,7 @@ def test_status_outcomes():
     with pytest.raises(LobpcgError) as e:
         s.solve(4, tol=1e-8, maxit=10)
     assert e.value.code == capi.ERR_NONFINITE
-    for bad in (0, 33, 300):
+    for bad in (0, 101, 300):
         with pytest.raises(LobpcgError) as e:
             s.solve(bad, tol=1e-8, maxit=10)
         assert e.value.code == capi.ERR_ARG
@@ -212,3 +212,30 @@ def test_call_order_and_allocator_failure():
     assert capi.lobpcg_solve(h, 4, 1e-8, 10, 2, None) == capi.ERR_OOM
     assert "allocation" in capi.lobpcg_last_error(h)
     assert capi.lobpcg_destroy(h) == capi.OK
+
+
+@pytest.mark.parametrize("dims,m", [((14, 13, 12), 40), ((12, 12, 11), 64)])
+def test_wide_blocks_match_oracle(dims, m):
+    """Blocks wider than 32 columns (Rayleigh-Ritz bases up to 3m = 192, the Gram split into
+    several thread blocks per row range, the Cholesky factors of 40..64 columns): eigenvalues
+    within 1e-10 of the oracle and of the dense eigenvalues, iterations within 10 %."""
+    tol, maxit = 1e-8, 300
+    s = Solver(dims, scale=1.0, levels=2)
+    out = s.solve(m, tol=tol, maxit=maxit, seed=2)
+    s.close()
+    ref = oracle_run(dims, 1.0, m, tol, maxit, 2)
+    assert out["status_name"] == "ok" and ref.status == "converged"
+    lam = np.array(out["lam"])
+    assert np.max(np.abs(lam - ref.lam) / ref.lam) < 1e-10
+    want = np.linalg.eigvalsh(laplace.dense_matrix(dims, 1.0))[:m]
+    assert np.max(np.abs(lam - want) / want) < 1e-10
+    assert within_10pct(out["iters"], ref.iters), (out["iters"], ref.iters)
+    assert out["max_rel_resid"] <= tol * (1 + 1e-6)
+
+
+def test_mixed_form_caps_the_block_at_32():
+    s = Solver((16, 16, 16), levels=3, precision="mixed")
+    with pytest.raises(LobpcgError) as e:
+        s.solve(33, tol=1e-8, maxit=10)
+    assert e.value.code == capi.ERR_ARG
+    s.close()
