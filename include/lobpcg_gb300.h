@@ -166,8 +166,18 @@ int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timin
  * LOBPCG_MIXED handle. */
 int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
 
-/* Engine of the float32 Gram products of the mixed form (steps 11, 15, 17-23;
- * the double-float X^T X block is unaffected):
+/* Engine of the Gram products.
+ * Float64 form (and the float64 steps of the mixed form): unless the engine is
+ * LOBPCG_ENGINE_SIMT, Gram matrices of at most 48 columns run on the tensor
+ * cores by error-free digit products: per window of 1024 grid points every
+ * column is split into 8 signed 7-bit digits under the window's largest
+ * exponent (bfloat16, exact), the digit-pair products are summed exactly by
+ * tcgen05 MMAs in float32 tensor memory, and the pairs are combined in 64-bit
+ * integers and added in float64 (Ozaki, Ogita and Oishi's error-free splitting;
+ * about 2^-48 of the window's largest products, float64 quality for smooth
+ * grid functions).  LOBPCG_ENGINE_SIMT keeps the float64 FMA pipe.
+ * Mixed form, float32 Gram products (steps 11, 15, 17-23; the double-float
+ * X^T X block is unaffected):
  *   LOBPCG_ENGINE_TENSOR: tcgen05 tensor-core MMAs on 3 x TF32 splits (hi*hi +
  *     hi*lo + lo*hi, about 2^-21 relative per product), float32 accumulation
  *     in tensor memory over at most 128 grid points (the tensor cores round it
@@ -182,7 +192,7 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
  *     columns (the residual-form Gram), the SIMT engine below that.  A tensor
  *     core MMA costs about the same for any N <= 256 on GB300, so the tensor
  *     form pays off only for wide stacks.
- * The float64 form ignores it.  Returns ERR_ARG for an unknown engine. */
+ * Returns ERR_ARG for an unknown engine. */
 #define LOBPCG_ENGINE_AUTO     0
 #define LOBPCG_ENGINE_SIMT     1
 #define LOBPCG_ENGINE_TENSOR   2
@@ -323,8 +333,10 @@ int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X,
  * Writes the q-by-q (q = w0 + w1 + w2) column-major device matrices gramB = S^T S
  * and gramA with the block structure printed in steps 18 / 21: block (I, J) =
  * S_I^T AS_J for I < J, its transpose below the diagonal, and (S_I^T AS_I +
- * AS_I^T S_I)/2 on the diagonal.  AS0 may be NULL (gramA skipped).
- * Deterministic: partial sums per thread block are added in a fixed order. */
+ * AS_I^T S_I)/2 on the diagonal.  AS0 may be NULL (gramA skipped).  The
+ * handle's Gram engine applies (tensor-core digit products for q <= 48 unless
+ * LOBPCG_ENGINE_SIMT).  Deterministic: partial sums per thread block are added
+ * in a fixed order.  Errors: ERR_ARG, ERR_TIMEOUT, ERR_CUDA. */
 int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double* S2,
                    const double* AS0, const double* AS1, const double* AS2,
                    int64_t ld, int w0, int w1, int w2, double* gramA, double* gramB);

@@ -139,6 +139,12 @@ int gram_parts(int64_t n, int q);
 int64_t gram_scratch_doubles(int64_t n, int q);
 void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int nparts,
                  cudaStream_t st);
+// The same partial sums (float64 blocks of at most 48 columns) on the tensor cores by error-free
+// bfloat16 digit products (k_gram_oz.cu); returns the number of row ranges (partials) written,
+// 0 if the scratch cannot hold them (nothing launched).
+bool gram_oz_fits(int q);
+int launch_gram_oz(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int64_t part_doubles,
+                   unsigned* status, cudaStream_t st);
 // gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
 // summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
 // diagonal blocks of gramB are identities (steps 18-22 as printed).

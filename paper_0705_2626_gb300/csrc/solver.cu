@@ -419,10 +419,24 @@ Blocks3 blocks(const void* p0, int w0, DType t0, const void* p1, int w1, const v
     return b;
 }
 
+// Float64 Gram on the tensor cores (error-free digit products) unless the SIMT engine is chosen
+// or the basis is wider than 48 columns.
+bool use_oz(const lobpcg_t* h, const Blocks3& S) {
+    const bool f64 = S.t0 == DT_F64 && (S.w[1] + S.w[2] == 0 || S.t12 == DT_F64);
+    return f64 && h->gram_engine != LOBPCG_ENGINE_SIMT && gram_oz_fits(S.q());
+}
+
 void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* gB,
           const double* paper_lam) {
     const int64_t n = h->g.n();
     const int q = S.q();
+    if (use_oz(h, S)) {
+        const int nparts = launch_gram_oz(n, S, AS, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+        if (nparts > 0) {
+            launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
+            return;
+        }
+    }
     const int nparts = (int)std::min<int64_t>(gram_parts(n, q), (int64_t)(h->part_doubles / (2 * (size_t)q * q)));
     LG_REQUIRE(nparts >= 1, LOBPCG_ERR_ARG, "Gram scratch too small");
     launch_gram(n, S, AS, f64(h->part), nparts, h->stream);
@@ -1465,8 +1479,12 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
         ensure_workspace(h, std::max(h->wm, (q + 2) / 3));
         const Blocks3 S = blocks(S0, w0, DT_F64, S1, w1, S2, w2, DT_F64, ld);
         const Blocks3 AS = blocks(AS0, w0, DT_F64, AS1, w1, AS2, w2, DT_F64, ld);
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
         gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         LG_CUDA(cudaStreamSynchronize(h->stream));
+        if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
         return LOBPCG_OK;
     });
 }

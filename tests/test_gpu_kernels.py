@@ -280,3 +280,55 @@ def test_rayleigh_ritz_breakdown_on_indefinite_gramB():
     lamd = torch.empty(4, dtype=torch.float64, device="cuda")
     Cd = torch.empty((4, 12), dtype=torch.float64, device="cuda")
     assert capi.lobpcg_op_rayleigh_ritz(s.h, 12, 4, ptr(Ad), ptr(Bd), ptr(lamd), ptr(Cd)) == capi.ERR_BREAKDOWN
+
+
+def _gram_b(s, S, engine):
+    capi.lobpcg_set_gram_engine(s.h, {"auto": capi.ENGINE_AUTO, "simt": capi.ENGINE_SIMT}[engine])
+    n, q = S.shape
+    Sd = dev(S)
+    gB = torch.empty((q, q), dtype=torch.float64, device="cuda")
+    assert capi.lobpcg_op_gram(s.h, ptr(Sd), None, None, None, None, None, n, q, 0, 0, None, ptr(gB)) == capi.OK
+    return gB.cpu().numpy().T
+
+
+def test_gram_tensor_digits_are_summed_exactly():
+    """Every digit of 1 - 2^-56 is 127, so a window of 1024 equal points drives every digit-pair
+    sum of the tensor-core Gram to 1024 * 127^2 = 16,516,096, just below 2^24; with the signs
+    alternating the partial sums swing over the whole range.  The float32 accumulators must keep
+    every unit: the entries must equal the float64 sums to rounding (a lost unit would show at
+    about 1e-7 relative).  64 x 64 x 40 points give every thread block at least one full
+    window."""
+    s = make((64, 64, 40), precond="none")
+    n = s.n
+    v = 1.0 - 2.0 ** -56
+    S = np.empty((n, 4))
+    S[:, 0] = v
+    S[:, 1] = v * np.where(np.arange(n) % 2, -1.0, 1.0)
+    S[:, 2] = v * np.where(np.arange(n) < n // 2, 1.0, -1.0)
+    S[:, 3] = np.random.default_rng(3).uniform(-1.0, 1.0, n)
+    G = _gram_b(s, S, "auto")
+    want = S.T @ S
+    assert np.max(np.abs(G - want)) <= 1e-14 * n
+
+
+@pytest.mark.parametrize("dims,q", [((48, 48, 48), 8), ((64, 64, 64), 24), ((40, 36, 34), 48), ((7, 5, 3), 3)])
+def test_gram_engines_agree_on_grid_functions(dims, q):
+    """Tensor-core digit products against the float64 FMA pipe on smooth grid functions (sine
+    modes plus noise, the kind of basis LOBPCG builds): both within float64 rounding of the
+    definition, to 1e-14 relative to |s_i| |s_j|."""
+    s = make(dims, precond="none")
+    n = s.n
+    g = np.random.default_rng(4)
+    nx, ny, nz = dims
+    ii, jj, kk = np.meshgrid(np.arange(1, nx + 1), np.arange(1, ny + 1), np.arange(1, nz + 1), indexing="ij")
+    cols = []
+    for c in range(q):
+        a, b, d = 1 + c % 3, 1 + (c // 3) % 3, 1 + c // 9
+        f = np.sin(a * np.pi * ii / (nx + 1)) * np.sin(b * np.pi * jj / (ny + 1)) * np.sin(d * np.pi * kk / (nz + 1))
+        cols.append(f.transpose(2, 1, 0).ravel() * 10.0 ** g.uniform(-3, 3) + 1e-3 * g.standard_normal(n))
+    S = np.stack(cols, axis=1)
+    nrm = np.linalg.norm(S, axis=0)
+    want = S.T @ S
+    for engine in ("auto", "simt"):
+        G = _gram_b(s, S, engine)
+        assert np.all(np.abs(G - want) <= 1e-13 * np.outer(nrm, nrm)), engine
