@@ -563,9 +563,9 @@ int launch_gram_oz(int64_t n, const Blocks3& S, const Blocks3* AS, double* part,
     }
     a.nmt = (8 * q + 127) / 128;
     // groups of right columns, each with an even share of the S columns and of the AS columns, at
-    // most 32 columns and at most 512 / (8 nmt) so that the accumulators of every A tile fit the
-    // 512 TMEM columns
-    const int jmax = std::min(kOzMaxJ, 512 / (8 * a.nmt));
+    // most 32 columns, and few enough that the accumulators of every A tile (8 lines per column,
+    // rounded up to 32) fit the 512 TMEM columns
+    const int jmax = std::min(kOzMaxJ, (512 / a.nmt) / 32 * 32 / 8);
     a.ngroups = (a.r + jmax - 1) / jmax;
     while (a.ngroups <= kOzMaxGroups) {
         bool fits = true;

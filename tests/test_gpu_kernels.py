@@ -162,7 +162,7 @@ def test_residual_and_norms(dims, m, cols):
                                          ((16, 16, 16), (4, 4, 0)), ((128, 128, 128), (16, 16, 16)),
                                          ((20, 20, 20), (32, 32, 32)), ((2, 3, 5), (7, 1, 2)),
                                          ((20, 19, 18), (50, 50, 50)), ((12, 12, 12), (100, 100, 100)),
-                                         ((64, 64, 64), (8, 0, 0))])
+                                         ((64, 64, 64), (8, 0, 0)), ((30, 30, 30), (16, 16, 12))])
 def test_gram_matches_definition(dims, widths):
     s = make(dims, precond="none")
     n = s.n
@@ -210,7 +210,7 @@ def test_gram_is_deterministic():
 
 
 @pytest.mark.parametrize("dims,b", [((20, 20, 20), 6), ((9, 9, 9), 1), ((32, 32, 32), 32), ((128, 128, 128), 16),
-                                   ((24, 24, 24), 100), ((40, 40, 40), 50)])
+                                   ((24, 24, 24), 100), ((40, 40, 40), 50), ((24, 24, 24), 44), ((30, 20, 25), 41)])
 def test_cholqr_matches_oracle(dims, b):
     s = make(dims, precond="none")
     n = s.n
