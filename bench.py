@@ -37,17 +37,19 @@ WORKLOADS = {
     "c2": dict(dims=(128, 128, 128), m=16, levels=6),
     "c3": dict(dims=(256, 256, 256), m=32, levels=7),
     "c4": dict(dims=(464, 464, 464), m=8, levels=8),
+    # the 464^3 workload's block size on a 128^3 grid (the size the per-kernel ncu captures use)
+    "s4": dict(dims=(128, 128, 128), m=8, levels=6),
 }
 
 # Time to tol: seeded starts, and timed solves per seed after one warm-up solve (medians over
 # both); fewer timed solves on the two largest grids.
 TTT_SEEDS = (2, 3, 4)
-TTT_RUNS = {"c1": 5, "c2": 5, "c3": 3, "c4": 3}
+TTT_RUNS = {"c1": 5, "c2": 5, "c3": 3, "c4": 3, "s4": 3}
 
 # The oracle's bounded sample for the CPU figures: one oracle iteration on a grid of the same m and
 # V-cycle whose point count the host finishes in seconds; the figure is scaled to the workload by
 # the ratio of point counts (every step of an iteration is O(n) at fixed m).
-CPU_SAMPLE = {"c1": "c1", "c2": "c2", "c3": "s3", "c4": "s4"}
+CPU_SAMPLE = {"c1": "c1", "c2": "c2", "c3": "s3", "c4": "s4", "s4": "s4"}
 SAMPLES = {"s3": dict(dims=(96, 96, 96), m=32, levels=5), "s4": dict(dims=(128, 128, 128), m=8, levels=6)}
 
 # FP64 peak of GB300 from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz.
@@ -64,9 +66,10 @@ def _measured_hbm():
 
 HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 
-# DRAM traffic per launch of the Gram kernel (steps 17-23) from one ncu capture, keyed by the
-# SHA-256 of the kernel source it was taken on; a changed source invalidates it (traffic = null).
-NCU_TRAFFIC = {("c2", "b4503c8be547e48c"): 1.617388e9 + 13.800192e6}
+# DRAM traffic of the Gram phase (k_oz_exponents + k_gram_oz, steps 17-23) per iteration, from one
+# ncu capture on the 128^3 grid scaled by the point count to the workload, keyed by the SHA-256 of
+# k_gram_oz.cu; a changed source invalidates it (traffic = null).
+NCU_TRAFFIC = {}
 
 
 def closed_form_eigenvalues(dims, scale, m):
@@ -151,15 +154,18 @@ def gram_flops_per_launch(n, m):
     return 2.0 * n * 2 * (q * (q + 1) // 2)
 
 
+def gram_bytes_per_launch(n, m):
+    """Compulsory bytes of steps 17-23 at b = m: the float64 blocks [X W P] and [AX AW AP]
+    (q = 3m columns each) read once, (2m + 4b) * 8 bytes per point."""
+    return 2.0 * 3 * m * 8 * n
+
+
 def kernel_source_hash():
-    """Hash of the k_gram kernel's source text (from its template line to the next kernel), the
-    key under which its ncu DRAM traffic is recorded: an edit of the kernel invalidates it, edits
-    elsewhere in the file do not."""
-    with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", "k_block.cu")) as f:
-        src = f.read()
-    a = src.rfind("template", 0, src.index("__global__ void __launch_bounds__(kGramMaxThreads)"))
-    b = src.index("__global__ void k_gram_finalize_mx(")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    """Hash of k_gram_oz.cu (the float64 Gram on the tensor cores and its exponent pass), the key
+    under which the Gram phase's ncu DRAM traffic is recorded: an edit of that file invalidates
+    it."""
+    with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", "k_gram_oz.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def level_points(dims, levels):
@@ -379,7 +385,8 @@ def run_ours(args, rank, world, local_rank):
     s64, t64, launches, ph64, clocks = timed_form("fp64", sampler)
     value = replica_throughput(args.steps, world, t64)
     gram_ms = ph64["gram"]
-    achieved = gram_flops_per_launch(n, m) / (gram_ms * 1e-3) / 1e12
+    achieved = gram_bytes_per_launch(n, m) / (gram_ms * 1e-3) / 1e9
+    fp64_equiv = gram_flops_per_launch(n, m) / (gram_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get((w, kernel_source_hash()))
     out64, ttt64 = time_to_tol(s64)
 
@@ -418,7 +425,7 @@ def run_ours(args, rank, world, local_rank):
 
     kern64 = dict(residual=frac(3 * 8 * n * m, ph64["residual"]), spmv=frac(2 * 8 * n * m, ph64["spmv"]),
                   vcycle=frac(vcycle_bytes(dims, levels, m, 8, 8), ph64["precond"]),
-                  gram=frac(2 * q * 8 * n, ph64["gram"]))
+                  gram=frac(2 * q * 8 * n, ph64["gram"]), update=frac((2 * q + 4 * m) * 8 * n, ph64["update"]))
     kernmx = dict(residual=frac(3 * 4 * n * m, phmx["residual"]), spmv=frac(2 * 4 * n * m, phmx["spmv"]),
                   vcycle=frac(vcycle_bytes(dims, levels, m, 4, 2), phmx["precond"]),
                   gram=frac((2 * q + 2 * m) * 4 * n, phmx["gram"]),
@@ -454,10 +461,11 @@ def run_ours(args, rank, world, local_rank):
                          fp64=ttt_brief(ttt64, out64), mixed=ttt_brief(tttmx, outmx),
                          mixed_speedup=rnd(ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"], 3),
                          max_rel_lambda_diff_mixed_vs_fp64=rnd(lam_diff, 2)),
-        roofline=dict(kernel="k_gram (steps 17-23, gramA and gramB upper triangles, float64)", bound="alu",
-                      achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=achieved / FP64_PEAK_TFLOPS,
-                      traffic=traffic,
-                      peak_source="FP64 pipe from unit counts and clocks (152 SMs x 4 flop/clk x 2.07 GHz)"),
+        roofline=dict(kernel="Gram phase, steps 17-23: k_oz_exponents + k_gram_oz + k_gram_finalize (float64 "
+                             "Gram by bfloat16 digit products on the tensor cores)", bound="hbm",
+                      achieved=achieved, peak=HBM_PEAK_GBS, unit="GB/s", frac=achieved / HBM_PEAK_GBS,
+                      traffic=traffic, algorithmic_bytes=gram_bytes_per_launch(n, m), peak_source=HBM_PEAK_SOURCE,
+                      fp64_equiv_tflops=fp64_equiv, fp64_pipe_tflops=FP64_PEAK_TFLOPS),
         mixed=dict(value=replica_throughput(args.steps, world, tmx), unit="iters/s", ms_per_step=tmx / args.steps,
                    dtype="f64+f32+bf16", gpu_launches=launches_mx,
                    phase_ms=dict((k, rnd(v)) for k, v in phmx.items()), hbm_frac=kernmx),
