@@ -341,6 +341,28 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
                    const double* AS0, const double* AS1, const double* AS2,
                    int64_t ld, int w0, int w1, int w2, double* gramA, double* gramB);
 
+/* Float64 Ritz update (Algorithm steps 25-33): with S = [S0 S1 S2] (widths w0,
+ * w1, w2; w1, w2 may be 0; n rows, leading dimension ld >= n) and the
+ * q-by-m coefficients C (q = w0 + w1 + w2, column-major, leading dimension q,
+ * device), writes Xout = S C and, if Pout != NULL, Pout = S1 C1 + S2 C2 (the
+ * rows of C below w0), m columns each with leading dimension ld.  Xout may be
+ * S0 and Pout may be S2 (in place).  Unless the engine is LOBPCG_ENGINE_SIMT,
+ * products with q <= 32 and at most 28 outputs (2m with Pout, m without) run on
+ * the tensor cores by error-free digit products: every grid point split into 8
+ * signed 7-bit bfloat16 digits under its largest exponent over the q columns,
+ * every column of C under its own, the digit levels s + t <= 8 summed exactly in
+ * float32 tensor memory and combined in 64-bit integers (error per output below
+ * (q + 4) 2^-54 max_k |S(p, k)| max_k |C(k, j)| plus the final rounding; needs
+ * an even ld and 16-byte aligned blocks); otherwise float64 FMAs.  The solver's
+ * own calls (the V R^-1 products of lobpcg_op_cholqr and of the iteration, and
+ * the update) first scale the columns of S by powers of two (from the rows of
+ * R^-1, or from the column maxima of the preceding Gram), so that badly scaled
+ * columns keep their relative accuracy.  Errors: ERR_ARG, ERR_TIMEOUT,
+ * ERR_CUDA. */
+int lobpcg_op_update(lobpcg_t* h, const double* S0, const double* S1, const double* S2,
+                     int64_t ld, int w0, int w1, int w2, int m, const double* C,
+                     double* Xout, double* Pout);
+
 /* Cholesky orthonormalisation (Algorithm steps 3, 11, 14-15): G = V^T V,
  * R = chol(G) computed on the unit-diagonal scaling of G, V <- V R^-1 and, if
  * AV != NULL, AV <- AV R^-1 (in place, device, b columns, leading dimension ld).

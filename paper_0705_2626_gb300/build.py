@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB_NAME = "liblobpcg_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_stencil.cu", "k_block.cu", "k_gram32.cu", "k_gram_tc.cu", "k_gram_oz.cu", "k_mixed.cu", "k_tsmm.cu", "k_varcoef.cu", "k_dense.cu", "k_pcg.cu", "k_rr.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["k_stencil.cu", "k_block.cu", "k_gram32.cu", "k_gram_tc.cu", "k_gram_oz.cu", "k_tsmm_oz.cu", "k_mixed.cu", "k_tsmm.cu", "k_varcoef.cu", "k_dense.cu", "k_pcg.cu", "k_rr.cu", "solver.cu", "noalloc.cu"]
 
 
 def nvcc():

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "lobpcg_op_gram_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_int64, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "lobpcg_op_cholqr": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int64]),
+    "lobpcg_op_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_int, c_int,
+                                 c_void_p, c_void_p, c_void_p]),
     "lobpcg_op_rayleigh_ritz": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lobpcg_gram_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
                                     c_int64, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
@@ -217,6 +219,10 @@ def lobpcg_op_gram_residual(h, Xh, Xl, W, P, R, AW, AP, ld, m, b, bp, lam, gramA
 
 def lobpcg_op_cholqr(h, b, V, AV, ld):
     return _call("lobpcg_op_cholqr", h, b, V, AV, ld)
+
+
+def lobpcg_op_update(h, S0, S1, S2, ld, w0, w1, w2, m, C, Xout, Pout):
+    return _call("lobpcg_op_update", h, S0, S1, S2, ld, w0, w1, w2, m, C, Xout, Pout)
 
 
 def lobpcg_op_rayleigh_ritz(h, q, m, gramA, gramB, lam, C):

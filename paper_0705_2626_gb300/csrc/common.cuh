@@ -143,8 +143,26 @@ void launch_gram(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, i
 // bfloat16 digit products (k_gram_oz.cu); returns the number of row ranges (partials) written,
 // 0 if the scratch cannot hold them (nothing launched).
 bool gram_oz_fits(int q);
+// colmax (device, may be null): the largest exponent field of every column of S, then of AS, over
+// all grid points.
 int launch_gram_oz(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int64_t part_doubles,
-                   unsigned* status, cudaStream_t st);
+                   unsigned* status, cudaStream_t st, int* colmax = nullptr);
+// Y = S C on the tensor cores by error-free bfloat16 digit products (k_tsmm_oz.cu), float64
+// blocks of at most 32 columns: output j < nx is S C(:, j) (to out0 + j ldout), output nx + j
+// (j < np) is the sum over rows k >= w0p of S(:, k) C(k, j) (to out1 + j ldout); C is q x nx,
+// column-major, leading dimension ldc, on the device.  Outputs may overwrite S in place.
+// Column k of S is scaled by 2^a_k and row k of C by 2^-a_k before the split (exact; the digit
+// frame of a grid point is then its largest scaled entry): TZ_SCALE_NONE a_k = 0;
+// TZ_SCALE_C_ROWS 2^a_k about the largest |C(k, .)| (V R^-1: equilibrates the columns of V);
+// TZ_SCALE_S_COLS 2^-a_k about the largest |S(., k)|, from sexp (device, the largest exponent
+// field of each column of S, e.g. from launch_gram_oz).
+// Skipped if *status & skip; a bounded wait that gives up sets ST_TIMEOUT.  Returns false
+// (nothing launched) for shapes outside the kernel's limits.
+enum { TZ_SCALE_NONE = 0, TZ_SCALE_C_ROWS = 1, TZ_SCALE_S_COLS = 2 };
+bool tsmm_oz_fits(int q, int nout);
+bool launch_tsmm_oz(int64_t n, const Blocks3& S, const double* C, int ldc, int nx, int np, int w0p, double* out0,
+                    double* out1, int64_t ldout, unsigned* status, unsigned skip, cudaStream_t st,
+                    int scale_mode = TZ_SCALE_NONE, const int* sexp = nullptr);
 // gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
 // summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
 // diagonal blocks of gramB are identities (steps 18-22 as printed).

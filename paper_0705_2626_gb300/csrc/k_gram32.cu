@@ -404,6 +404,30 @@ void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t
 }
 
 
+void encode_f64_cols(CUtensorMap* map, const double* p, int64_t n, int w, int64_t ld, int box_rows) {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    LG_REQUIRE(g_encode, LOBPCG_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    LG_REQUIRE((reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 2 == 0, LOBPCG_ERR_ARG,
+               "float64 blocks must be 16-byte aligned with an even leading dimension");
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)w};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(double)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)w};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(p), dims, strides, box,
+                                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    LG_REQUIRE(r == CUDA_SUCCESS, LOBPCG_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
+
 void launch_gram_sub_ctc(int w, int b, const double* C, int ldc, double* G, cudaStream_t st) {
     if (b <= 0 || w <= 0) return;
     k_sub_ctc<<<(unsigned)ceil_div((int64_t)b * b, 256), 256, 0, st>>>(w, b, C, ldc, G);

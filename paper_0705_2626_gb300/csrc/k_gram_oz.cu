@@ -45,6 +45,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "oz_digits.cuh"
 #include "tma.cuh"
 
 namespace lg {
@@ -81,8 +82,10 @@ struct OzArgs {
 };
 
 // Largest exponent field of each R column over each exponent window: one warp per (window,
-// column), the high words of the column's values.
-__global__ void __launch_bounds__(256) k_oz_exponents(const __grid_constant__ OzArgs a, int* __restrict__ ex) {
+// column), the high words of the column's values.  colmax (may be null): the largest over all
+// windows, per column (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_oz_exponents(const __grid_constant__ OzArgs a, int* __restrict__ ex,
+                                                      int* __restrict__ colmax) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.y * 8 + warp;
     if (c >= a.r) return;
@@ -101,7 +104,10 @@ __global__ void __launch_bounds__(256) k_oz_exponents(const __grid_constant__ Oz
         for (int k = 0; k < 16; ++k) mx = max(mx, (hw[k] >> 20) & 0x7FF);
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) ex[(int64_t)blockIdx.x * a.r + c] = mx;
+    if (lane == 0) {
+        ex[(int64_t)blockIdx.x * a.r + c] = mx;
+        if (colmax) atomicMax(colmax + c, mx);
+    }
 }
 
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
@@ -177,27 +183,6 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[3
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// The 8 digits of x in the window frame of the column's largest exponent field emax, as
-// bfloat16 values (exact integers |d| <= 127 with the sign of x).
-__device__ __forceinline__ void split_digits(double x, int emax, float (&d)[kOzDigits]) {
-    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const int e = (hi >> 20) & 0x7FF;
-    uint64_t F = 0;
-    if (e != 0) {
-        const uint64_t M = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;   // 53-bit magnitude
-        const int sh = emax - e - 3;                                               // M 2^-sh = |x| 2^(56 - E)
-        // rounded to the nearest unit 2^(E - 56) (below the largest exponent only: F < 2^53 there)
-        F = sh <= 0 ? (M << (-sh)) : (sh < 64 ? (M + (1ull << (sh - 1))) >> sh : 0ull);
-    }
-    const uint32_t sgn = hi & 0x80000000u;
-#pragma unroll
-    for (int s = 0; s < kOzDigits; ++s) {
-        const uint32_t u = (uint32_t)(F >> (49 - 7 * s)) & 127u;
-        const float f = __uint_as_float(0x4B000000u | u) - 8388608.0f;              // u, exactly
-        d[s] = __uint_as_float(__float_as_uint(f) | sgn);
-    }
-}
 
 // NF: float64 stages in the copy ring (NF - 1 stages of copies in flight ahead of the split).
 template <int NF>
@@ -341,14 +326,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 const double x0 = p0 < r1 ? fsrc[u * kOzStagePts] : 0.0;
                 const double x1 = p0 + 1 < r1 ? fsrc[u * kOzStagePts + 1] : 0.0;
                 float d0[kOzDigits], d1[kOzDigits];
-                split_digits(x0, e[u], d0);
-                split_digits(x1, e[u], d1);
+                oz_digits(x0, e[u], d0);
+                oz_digits(x1, e[u], d1);
                 unsigned char* pa = coffa[u] >= 0 ? sst + coffa[u] : nullptr;
                 unsigned char* pb = coffb[u] >= 0 ? sst + coffb[u] : nullptr;
 #pragma unroll
                 for (int s = 0; s < kOzDigits; ++s) {
-                    const __nv_bfloat162 v = __floats2bfloat162_rn(d0[s], d1[s]);
-                    const uint32_t bits = *reinterpret_cast<const uint32_t*>(&v);
+                    const uint32_t bits = oz_pack2(d0[s], d1[s]);
                     if (pa) *reinterpret_cast<uint32_t*>(pa + soff[s]) = bits;
                     if (pb) *reinterpret_cast<uint32_t*>(pb + soff[s]) = bits;
                 }
@@ -543,7 +527,7 @@ void launch_oz(const OzArgs& a, dim3 grid, size_t smem, double* part, unsigned* 
 bool gram_oz_fits(int q) { return q >= 1 && q <= kOzMaxQ; }
 
 int launch_gram_oz(int64_t n, const Blocks3& S, const Blocks3* AS, double* part, int64_t part_doubles,
-                   unsigned* status, cudaStream_t st) {
+                   unsigned* status, cudaStream_t st, int* colmax) {
     const int q = S.q();
     LG_REQUIRE(gram_oz_fits(q) && S.t0 == DT_F64 && (S.w[1] + S.w[2] == 0 || S.t12 == DT_F64), LOBPCG_ERR_ARG,
                "tensor-core float64 Gram: float64 basis of at most 48 columns");
@@ -619,7 +603,8 @@ int launch_gram_oz(int64_t n, const Blocks3& S, const Blocks3* AS, double* part,
     a.part_stride = 2 * q2;
     const size_t smem = fixed + (size_t)a.nstage * stage_bytes + (size_t)nf * fstage_bytes;
     LG_REQUIRE(smem <= 227 * 1024, LOBPCG_ERR_ARG, "tensor-core float64 Gram: shared memory");
-    k_oz_exponents<<<dim3((unsigned)nexpw, (unsigned)((a.r + 7) / 8)), 256, 0, st>>>(a, ex);
+    if (colmax) LG_CUDA(cudaMemsetAsync(colmax, 0, sizeof(int) * a.r, st));
+    k_oz_exponents<<<dim3((unsigned)nexpw, (unsigned)((a.r + 7) / 8)), 256, 0, st>>>(a, ex, colmax);
     LG_CHECK_LAUNCH();
     const dim3 grid((unsigned)nchunks, (unsigned)a.ngroups);
     switch (nf) {

@@ -92,6 +92,8 @@ struct lobpcg_handle {
     Buf part;          // Gram / residual partial sums
     Buf small;         // gramA, gramB, C, lam, Rinv, norms, rr work
     unsigned* status = nullptr;
+    int* colexp = nullptr;     // largest exponent field of each column of the last tensor-core Gram's [S AS]
+    int colexp_q = 0;          // its q (0: no valid record)
     size_t part_doubles = 0;
     double *gramA = nullptr, *gramB = nullptr, *Cm = nullptr, *lam = nullptr, *Rinv = nullptr,
            *norms = nullptr, *rrwork = nullptr, *Gsmall = nullptr;
@@ -175,6 +177,8 @@ void free_workspace(lobpcg_t* h) {
     h->lt.clear();
     h->wm = 0;
     h->status = nullptr;
+    h->colexp = nullptr;
+    h->colexp_q = 0;
 }
 
 void free_varcoef(lobpcg_t* h) {
@@ -221,7 +225,7 @@ void ensure_workspace(lobpcg_t* h, int wm) {
         std::max<int64_t>(residual_chunks(n), resid_mx_blocks(h->g)) * wm);
     ensure(h, h->part, h->part_doubles * sizeof(double));
     const size_t nsmall = 2 * (size_t)q * q + (size_t)q * wm + wm + (size_t)wm * wm + wm +
-                          (size_t)rr_work_doubles(q) + (size_t)wm * wm + 8;
+                          (size_t)rr_work_doubles(q) + (size_t)wm * wm + 8 + (size_t)q + 8;
     ensure(h, h->small, nsmall * sizeof(double));
     double* s = f64(h->small);
     h->gramA = s; s += (size_t)q * q;
@@ -233,6 +237,8 @@ void ensure_workspace(lobpcg_t* h, int wm) {
     h->rrwork = s; s += rr_work_doubles(q);
     h->Gsmall = s; s += (size_t)wm * wm;
     h->status = (unsigned*)s;
+    h->colexp = reinterpret_cast<int*>(s + 8);           // 2 q ints
+    h->colexp_q = 0;
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     h->wm = wm;
 }
@@ -426,13 +432,48 @@ bool use_oz(const lobpcg_t* h, const Blocks3& S) {
     return f64 && h->gram_engine != LOBPCG_ENGINE_SIMT && gram_oz_fits(S.q());
 }
 
+// Float64 Y = S C for a tall block S and a small C on the tensor cores (error-free digit products)
+// unless the SIMT engine is chosen or the shape is outside the kernel's limits; false if the
+// caller must run the float64 FMA kernel instead.
+bool tsmm_f64(lobpcg_t* h, const Blocks3& S, const double* C, int ldc, int nx, int np, int w0p, double* out0,
+              double* out1, unsigned skip, int scale_mode, const int* sexp) {
+    return h->gram_engine != LOBPCG_ENGINE_SIMT &&
+           launch_tsmm_oz(h->g.n(), S, C, ldc, nx, np, w0p, out0, out1, S.ld, h->status, skip, h->stream, scale_mode,
+                          sexp);
+}
+
+// Float64 Ritz update (steps 25-33): Pout = S_1 C_1 + S_2 C_2 (rows >= w0 of C = h->Cm) if Pout is
+// not null, and Xout = S C (outputs with the leading dimension of S); in place over S_0 / S_2
+// allowed.  side: 0 for S = [X W P], 1 for [AX AW AP]; when the last Gram (steps 17-23) ran on the
+// tensor cores over this basis, its column exponents equilibrate the columns (AX, AW and AP may
+// differ in scale by orders of magnitude).
+void update_f64(lobpcg_t* h, int m, const Blocks3& S, double* Xout, double* Pout, unsigned skip, int side) {
+    const int q = S.q();
+    const bool have = h->colexp_q == q;
+    if (!tsmm_f64(h, S, h->Cm, q, m, Pout ? m : 0, S.w[0], Xout, Pout, skip, have ? TZ_SCALE_S_COLS : TZ_SCALE_NONE,
+                  have ? h->colexp + side * q : nullptr))
+        launch_update(h->g.n(), m, S, h->Cm, Xout, Pout, S.ld, h->status, skip, h->stream);
+}
+
+// V <- V Rinv (float64, b columns, in place; Rinv b x b upper triangular on the device).  The
+// columns of V are equilibrated by the rows of Rinv (R^-1 = D R'^-1 with D the inverse column
+// norms), which keeps the product invariant under column scaling of V (Section 2.2).
+void apply_rinv_f64(lobpcg_t* h, int b, double* V, const double* Rinv, unsigned skip) {
+    const Blocks3 SV = blocks(V, b, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
+    if (!tsmm_f64(h, SV, Rinv, b, b, 0, 0, V, nullptr, skip, TZ_SCALE_C_ROWS, nullptr))
+        launch_apply_rinv(h->g.n(), b, DT_F64, V, h->ld, V, h->ld, Rinv, h->status, skip, h->stream);
+}
+
 void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* gB,
           const double* paper_lam) {
     const int64_t n = h->g.n();
     const int q = S.q();
+    h->colexp_q = 0;
     if (use_oz(h, S)) {
-        const int nparts = launch_gram_oz(n, S, AS, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream);
+        const int nparts = launch_gram_oz(n, S, AS, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream,
+                                          AS ? h->colexp : nullptr);
         if (nparts > 0) {
+            if (AS) h->colexp_q = q;
             launch_gram_finalize(q, nparts, f64(h->part), AS != nullptr, gA, gB, paper_lam, &S, h->stream);
             return;
         }
@@ -486,7 +527,7 @@ void apply_rinv(lobpcg_t* h, int b, DType t, void* V, unsigned skip) {
     if (t == DT_F32)
         launch_apply32(h->g.n(), b, static_cast<float*>(V), h->ld, h->Rinv, h->status, skip, h->status, h->stream);
     else
-        launch_apply_rinv(h->g.n(), b, t, V, h->ld, V, h->ld, h->Rinv, h->status, skip, h->stream);
+        apply_rinv_f64(h, b, static_cast<double*>(V), h->Rinv, skip);
 }
 
 // G = V^T V for the Cholesky orthonormalisation of a W / P block (steps 11 and 13).
@@ -635,7 +676,7 @@ void prepare_constraints(lobpcg_t* h) {
             const Blocks3 S = blocks(Yk, k, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
             gram(h, S, nullptr, h->gramA, h->gramB, nullptr);
             launch_chol_rinv(k, h->gramB, h->gramA, h->status, ST_X_BREAKDOWN, 0u, st);
-            launch_apply_rinv(n, k, DT_F64, Yk, h->ld, Yk, h->ld, h->gramA, h->status, ST_X_BREAKDOWN, st);
+            apply_rinv_f64(h, k, Yk, h->gramA, ST_X_BREAKDOWN);
         }
     }
     unsigned stw = 0;
@@ -659,7 +700,7 @@ void orthonormalize_and_rr(lobpcg_t* h) {
     const Blocks3 SX = blocks(h->X.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
     gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr);
     launch_chol_rinv(m, h->Gsmall, h->Rinv, h->status, ST_X_BREAKDOWN, 0u, st);
-    launch_apply_rinv(n, m, DT_F64, h->X.p, h->ld, h->X.p, h->ld, h->Rinv, h->status, ST_X_BREAKDOWN, st);
+    apply_rinv_f64(h, m, f64(h->X), h->Rinv, ST_X_BREAKDOWN);
     spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
     const Blocks3 SAX = blocks(h->AX.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
     gram(h, SX, &SAX, h->gramA, h->gramB, nullptr);
@@ -668,8 +709,9 @@ void orthonormalize_and_rr(lobpcg_t* h) {
     const unsigned skip = ST_X_BREAKDOWN | ST_RR_BREAKDOWN;
     float* xh = h->precision == LOBPCG_MIXED ? static_cast<float*>(h->Xh.p) : nullptr;
     float* xl = h->precision == LOBPCG_MIXED ? static_cast<float*>(h->Xl.p) : nullptr;
-    launch_update(n, m, SX, h->Cm, f64(h->X), nullptr, h->ld, h->status, skip, st, xh, xl);
-    launch_update(n, m, SAX, h->Cm, f64(h->AX), nullptr, h->ld, h->status, skip, st);
+    if (xh) launch_update(n, m, SX, h->Cm, f64(h->X), nullptr, h->ld, h->status, skip, st, xh, xl);
+    else update_f64(h, m, SX, f64(h->X), nullptr, skip, 0);
+    update_f64(h, m, SAX, f64(h->AX), nullptr, skip, 1);
     h->J.resize(m);
     for (int j = 0; j < m; ++j) h->J[j] = j;
     residual_into_W(h);
@@ -842,7 +884,7 @@ void pass_body(lobpcg_t* h) {
             // AP_J so much that AP_J R^-1 no longer matches A (P_J R^-1).
             spmv(h, b, tw, Pj, ld, APj, ld);
         } else {
-            launch_apply_rinv(n, b, tw, APj, ld, APj, ld, h->Rinv, h->status, ST_W_BREAKDOWN | ST_P_DROPPED, st);
+            apply_rinv_f64(h, b, static_cast<double*>(APj), h->Rinv, ST_W_BREAKDOWN | ST_P_DROPPED);
         }
     }
     tm.mark(4);
@@ -873,8 +915,8 @@ void pass_body(lobpcg_t* h) {
                           static_cast<const float*>(h->W.p), b, static_cast<const float*>(Pj), use_p ? b : 0, ld,
                           h->Cm, q, static_cast<float*>(h->P.p), h->status, skip, h->status, st);
     } else {
-        launch_update(n, m, S, h->Cm, f64(h->X), h->P.p, ld, h->status, skip, st);
-        launch_update(n, m, AS, h->Cm, f64(h->AX), h->AP.p, ld, h->status, skip, st);
+        update_f64(h, m, S, f64(h->X), f64(h->P), skip, 0);
+        update_f64(h, m, AS, f64(h->AX), f64(h->AP), skip, 1);
     }
     tm.mark(7);
     // step 7 of the next pass
@@ -1546,13 +1588,42 @@ int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld) {
         const Blocks3 SV = blocks(V, b, DT_F64, nullptr, 0, nullptr, 0, DT_F64, ld);
         gram(h, SV, nullptr, h->gramA, h->Gsmall, nullptr);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
-        launch_apply_rinv(n, b, DT_F64, V, ld, V, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
-        if (AV) launch_apply_rinv(n, b, DT_F64, AV, ld, AV, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        if (ld == h->ld) {
+            apply_rinv_f64(h, b, V, h->Rinv, ST_W_BREAKDOWN);
+            if (AV) apply_rinv_f64(h, b, AV, h->Rinv, ST_W_BREAKDOWN);
+        } else {
+            launch_apply_rinv(n, b, DT_F64, V, ld, V, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+            if (AV) launch_apply_rinv(n, b, DT_F64, AV, ld, AV, ld, h->Rinv, h->status, ST_W_BREAKDOWN, st);
+        }
         unsigned stw = 0;
         LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         LG_CUDA(cudaStreamSynchronize(st));
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
         if (stw & ST_W_BREAKDOWN) throw Error(LOBPCG_ERR_BREAKDOWN, "Gram matrix not positive definite");
+        return LOBPCG_OK;
+    });
+}
+
+int lobpcg_op_update(lobpcg_t* h, const double* S0, const double* S1, const double* S2, int64_t ld, int w0,
+                     int w1, int w2, int m, const double* C, double* Xout, double* Pout) {
+    return guarded(h, [&] {
+        require_op(h);
+        const int64_t n = h->g.n();
+        const int q = w0 + w1 + w2;
+        LG_REQUIRE(S0 && C && Xout && w0 >= 1 && w1 >= 0 && w2 >= 0 && q <= 3 * LOBPCG_MAX_M && m >= 1 &&
+                       m <= LOBPCG_MAX_M && (w1 == 0 || S1) && (w2 == 0 || S2) && valid_ld(ld, n),
+                   LOBPCG_ERR_ARG, "invalid update arguments");
+        ensure_workspace(h, std::max(h->wm, std::max(m, (q + 2) / 3)));
+        const Blocks3 S = blocks(S0, w0, DT_F64, S1, w1, S2, w2, DT_F64, ld);
+        LG_CUDA(cudaMemcpyAsync(h->Cm, C, sizeof(double) * (size_t)q * m, cudaMemcpyDeviceToDevice, h->stream));
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        h->colexp_q = 0;                 // no Gram of this basis: the plain frame per grid point
+        update_f64(h, m, S, Xout, Pout, 0u, 0);
+        unsigned stw = 0;
+        LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        LG_CUDA(cudaStreamSynchronize(h->stream));
+        LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+        if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
         return LOBPCG_OK;
     });
 }

@@ -1,5 +1,5 @@
 // Inline PTX for the Tensor Memory Accelerator and shared-memory mbarriers, shared by the
-// TMA-staged kernels (k_gram32.cu, k_tsmm.cu), and the host-side tensor-map encoder.
+// TMA-staged kernels (k_gram32.cu, k_tsmm.cu, k_tsmm_oz.cu), and the host-side tensor-map encoders.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -15,6 +15,9 @@ extern thread_local int g_wait_limit;   // run-time poll limit of the stage wait
 // c ^ (r mod 8)).
 void encode_f32_cols(CUtensorMap* map, const float* p, int64_t n, int w, int64_t ld, int box_rows,
                      bool swizzle128 = false);
+// Column blocks of float64 (16-byte aligned, even leading dimension) as a 2-D tensor map with
+// boxes of box_rows x w, no swizzle (column c of the box box_rows doubles after column c - 1).
+void encode_f64_cols(CUtensorMap* map, const double* p, int64_t n, int w, int64_t ld, int box_rows);
 
 namespace {
 
