@@ -170,13 +170,14 @@ __device__ __forceinline__ double scaled_to_double(long long t, int ex) {
 }
 
 // One output from its nine levels D_0..D_8 (exact float32 integers, |D| < 2^22):
-// T = sum_L D_L 2^(7 (8 - L)), result = floor(T / 2^14) 2^(E_p + F_j - 56) rounded to float64
-// (the dropped 14 bits lie 2^-56 below max |S(p, .)| max |C(., j)|).  ex = E_p + F_j - 56.
+// T = sum_L D_L 2^(7 (8 - L)), result = round(T / 2^14) 2^(E_p + F_j - 56) rounded to float64
+// (the 14 bits rounded off lie 2^-57 below max |S(p, .)| max |C(., j)|; rounding to nearest
+// rather than down keeps the outputs free of a common bias).  ex = E_p + F_j - 56.
 __device__ __forceinline__ double combine_levels(const float (&D)[kTzLevels], int ex) {
     int i[kTzLevels];
 #pragma unroll
     for (int L = 0; L < kTzLevels; ++L) i[L] = __float_as_int(D[L] + 12582912.0f) - 0x4B400000;
-    const int lo14 = i[5] * 128 + i[6] + ((i[7] * 128 + i[8]) >> 14);   // arithmetic shift: floor
+    const int lo14 = i[5] * 128 + i[6] + ((i[7] * 128 + i[8] + 8192) >> 14);   // floor(x + 1/2)
     const int a1 = i[0] * 128 + i[1];
     const int a2 = i[2] * 128 + i[3];
     const long long t = (long long)a1 * (1ll << 35) + (long long)a2 * (1ll << 21) + (long long)i[4] * (1ll << 14) +
