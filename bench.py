@@ -69,7 +69,7 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 # DRAM traffic of the Gram phase (k_oz_exponents + k_gram_oz, steps 17-23) per iteration, from one
 # ncu capture on the 128^3 grid scaled by the point count to the workload, keyed by the SHA-256 of
 # k_gram_oz.cu; a changed source invalidates it (traffic = null).
-NCU_TRAFFIC = {("c4", "ced549b648fa42cc"): ((805.883648e6 + 6.001920e6) + (805.321216e6 + 2.976256e6)) * 99897344 / 2097152}
+NCU_TRAFFIC = {}
 
 
 def closed_form_eigenvalues(dims, scale, m):
@@ -161,11 +161,14 @@ def gram_bytes_per_launch(n, m):
 
 
 def kernel_source_hash():
-    """Hash of k_gram_oz.cu (the float64 Gram on the tensor cores and its exponent pass), the key
-    under which the Gram phase's ncu DRAM traffic is recorded: an edit of that file invalidates
-    it."""
-    with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", "k_gram_oz.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of k_gram_oz.cu and oz_digits.cuh (the float64 Gram on the tensor cores, its exponent
+    pass and its digit split), the key under which the Gram phase's ncu DRAM traffic is recorded:
+    an edit of either file invalidates it."""
+    h = hashlib.sha256()
+    for name in ("k_gram_oz.cu", "oz_digits.cuh"):
+        with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def level_points(dims, levels):

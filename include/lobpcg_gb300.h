@@ -168,8 +168,10 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
 
 /* Engine of the Gram products.
  * Float64 form (and the float64 steps of the mixed form): unless the engine is
- * LOBPCG_ENGINE_SIMT, Gram matrices of at most 48 columns run on the tensor
- * cores by error-free digit products: per window of 1024 grid points every
+ * LOBPCG_ENGINE_SIMT, the Gram matrices of steps 17-23 (and those of
+ * lobpcg_op_gram) with at most 48 columns run on the tensor cores by error-free
+ * digit products (the Cholesky Grams of single blocks, whose factor decides a
+ * breakdown, stay on the float64 pipe): per window of 1024 grid points every
  * column is split into 8 signed 7-bit digits under the window's largest
  * exponent (bfloat16, exact), the digit-pair products are summed exactly by
  * tcgen05 MMAs in float32 tensor memory, and the pairs are combined in 64-bit

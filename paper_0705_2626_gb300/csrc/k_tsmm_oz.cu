@@ -152,21 +152,21 @@ __device__ __forceinline__ uint4 digits8(double x, int emax) {
     return make_uint4(oz_pack2(d[0], d[1]), oz_pack2(d[2], d[3]), oz_pack2(d[4], d[5]), oz_pack2(d[6], d[7]));
 }
 
-// t 2^ex rounded to float64 (nearest, ties to even) by integer operations only; results below
-// the normal range are flushed to zero.
+// t 2^ex rounded to float64 (nearest, ties to even) by integer operations only, without branches;
+// results below the normal range are flushed to zero.
 __device__ __forceinline__ double scaled_to_double(long long t, int ex) {
-    if (t == 0) return 0.0;
     const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
-    unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
-    const int lz = __clzll((long long)a);
-    a <<= lz;                                          // leading one at bit 63
-    const unsigned long long rest = a & 0x7FFull;
-    unsigned long long mant = a >> 11;                 // 53 bits, leading one at bit 52
+    const unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+    const int lz = __clzll((long long)(a | 1ull));
+    const unsigned long long top = a << lz;            // leading one at bit 63 (t != 0)
+    const unsigned long long rest = top & 0x7FFull;
+    unsigned long long mant = top >> 11;               // 53 bits, leading one at bit 52
     mant += (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
     const int eb = 63 - lz + ex + 1023;                // biased exponent of the leading one
-    if (eb <= 0) return __longlong_as_double((long long)sgn);
-    if (eb >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-    return __longlong_as_double((long long)(sgn | (((unsigned long long)(eb - 1) << 52) + mant)));
+    unsigned long long bits = sgn | (((unsigned long long)(eb - 1) << 52) + mant);
+    bits = eb >= 2047 ? (sgn | 0x7FF0000000000000ull) : bits;
+    bits = (eb <= 0 || t == 0) ? sgn : bits;
+    return __longlong_as_double((long long)bits);
 }
 
 // One output from its nine levels D_0..D_8 (exact float32 integers, |D| < 2^22):
@@ -321,18 +321,17 @@ __global__ void __launch_bounds__(kTzThreads, 1) k_tsmm_oz(const __grid_constant
                 break;
             }
             const double* stg = sF + (size_t)fs * f_doubles + p;
-            // frame of the grid point: its largest scaled exponent field
-            int em = -kTzOff;
-            bool bad = false;
+            // frame of the grid point: its largest scaled exponent field (zeros take no part)
+            int em = -kTzOff, eraw = 0;
 #pragma unroll 8
             for (int k = 0; k < a.q; ++k) {
                 const int e = (reinterpret_cast<const int*>(stg + k * kTzTile)[1] >> 20) & 0x7FF;
-                bad |= e == 2047;
-                if (e != 0) em = max(em, e + aoff[k]);
+                eraw = max(eraw, e);
+                em = max(em, e != 0 ? e + aoff[k] : -kTzOff);
             }
-            ep[(t % kTzEpRing) * kTzTile + p] = bad ? kTzNaN : em;
+            ep[(t % kTzEpRing) * kTzTile + p] = eraw == 2047 ? kTzNaN : em;
             unsigned char* stA = sA + (size_t)as * a.a_bytes;
-#pragma unroll 4
+#pragma unroll 8
             for (int k = 0; k < a.q2; ++k) {
                 const double x = k < a.q ? stg[k * kTzTile] : 0.0;
                 *reinterpret_cast<uint4*>(stA + chunk_off(p, k, kTzTile)) = digits8(x, k < a.q ? em - aoff[k] : 0);

@@ -22,11 +22,12 @@ __device__ __forceinline__ void oz_digits(double x, int emax, float (&d)[8]) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const int e = (int)((hi >> 20) & 0x7FFu);
     const int sh = emax - e;
-    uint64_t F = 0;
-    if (e != 0 && sh < 60) {
-        const uint64_t M3 = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 3;   // |x| 2^(56-E) 2^sh
-        F = sh == 0 ? M3 : (M3 + (1ull << (sh - 1))) >> sh;                               // rounded to nearest
-    }
+    // |x| 2^(56 - E) = M3 2^-sh, rounded to nearest (no branch: sh is clamped, the zero and
+    // far-below-frame cases are selected away)
+    const uint64_t M3 = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 3;
+    const int s = min(max(sh, 0), 63);
+    uint64_t F = (M3 + ((1ull << s) >> 1)) >> s;
+    F = (e == 0 || sh >= 60) ? 0ull : F;
     const uint32_t fh = (uint32_t)(F >> 32), fl = (uint32_t)F;
     const float sg = __uint_as_float((hi & 0x80000000u) | 0x3F800000u);   // sign(x) as +-1
     const float nb = -8388608.0f * sg;                                    // -2^23 sign(x)

@@ -464,12 +464,17 @@ void apply_rinv_f64(lobpcg_t* h, int b, double* V, const double* Rinv, unsigned 
         launch_apply_rinv(h->g.n(), b, DT_F64, V, h->ld, V, h->ld, Rinv, h->status, skip, h->stream);
 }
 
+// Gram matrices of S (and S^T AS).  tensor: the tensor-core digit products may serve (the Grams
+// of steps 17-23); the Cholesky Grams of single blocks pass false and stay on the float64 pipe:
+// their factor decides breakdown (R9) and is inverted, and the tensor Grams' errors, relative to
+// each window's largest entries, are coarser than those of float64 sums on the nearly dependent
+// blocks near convergence (a 128^3, m = 48 solve broke down on W_J with them, converged without).
 void gram(lobpcg_t* h, const Blocks3& S, const Blocks3* AS, double* gA, double* gB,
-          const double* paper_lam) {
+          const double* paper_lam, bool tensor) {
     const int64_t n = h->g.n();
     const int q = S.q();
     h->colexp_q = 0;
-    if (use_oz(h, S)) {
+    if (tensor && use_oz(h, S)) {
         const int nparts = launch_gram_oz(n, S, AS, f64(h->part), (int64_t)h->part_doubles, h->status, h->stream,
                                           AS ? h->colexp : nullptr);
         if (nparts > 0) {
@@ -537,7 +542,7 @@ void block_gram(lobpcg_t* h, int b, DType t, const void* V, double* G) {
                             f64(h->part), (int64_t)h->part_doubles, h->status, use_tc(h), h->stream);
     } else {
         const Blocks3 S = blocks(V, b, t, nullptr, 0, nullptr, 0, t, h->ld);
-        gram(h, S, nullptr, h->gramA, G, nullptr);
+        gram(h, S, nullptr, h->gramA, G, nullptr, false);
     }
 }
 
@@ -628,7 +633,7 @@ void free_constraints(lobpcg_t* h) {
 // V <- V - Qc (Qc^T V) for one chunk Qc (k columns) of the float64 basis; V float64, b columns.
 void project_chunk64(lobpcg_t* h, int b, double* V, const double* Qc, int k) {
     const Blocks3 S = blocks(V, b, DT_F64, Qc, k, nullptr, 0, DT_F64, h->ld);
-    gram(h, S, nullptr, h->gramA, h->gramB, nullptr);            // gramB = [V Qc]^T [V Qc]
+    gram(h, S, nullptr, h->gramA, h->gramB, nullptr, false);     // gramB = [V Qc]^T [V Qc]
     launch_proj_coef(b, k, h->gramB, h->gramA, h->stream);       // gramA <- [I; -Qc^T V]
     launch_update(h->g.n(), b, S, h->gramA, V, nullptr, h->ld, nullptr, 0u, h->stream);
 }
@@ -674,7 +679,7 @@ void prepare_constraints(lobpcg_t* h) {
                 project_chunk64(h, k, Yk, static_cast<const double*>(col(h->Yq, DT_F64, h->ld, j0)),
                                 std::min(kc, c0 - j0));
             const Blocks3 S = blocks(Yk, k, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
-            gram(h, S, nullptr, h->gramA, h->gramB, nullptr);
+            gram(h, S, nullptr, h->gramA, h->gramB, nullptr, false);
             launch_chol_rinv(k, h->gramB, h->gramA, h->status, ST_X_BREAKDOWN, 0u, st);
             apply_rinv_f64(h, k, Yk, h->gramA, ST_X_BREAKDOWN);
         }
@@ -698,12 +703,12 @@ void orthonormalize_and_rr(lobpcg_t* h) {
     const int m = h->m;
     cudaStream_t st = h->stream;
     const Blocks3 SX = blocks(h->X.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
-    gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr);
+    gram(h, SX, nullptr, h->gramA, h->Gsmall, nullptr, false);
     launch_chol_rinv(m, h->Gsmall, h->Rinv, h->status, ST_X_BREAKDOWN, 0u, st);
     apply_rinv_f64(h, m, f64(h->X), h->Rinv, ST_X_BREAKDOWN);
     spmv(h, m, DT_F64, h->X.p, h->ld, h->AX.p, h->ld);
     const Blocks3 SAX = blocks(h->AX.p, m, DT_F64, nullptr, 0, nullptr, 0, DT_F64, h->ld);
-    gram(h, SX, &SAX, h->gramA, h->gramB, nullptr);
+    gram(h, SX, &SAX, h->gramA, h->gramB, nullptr, true);
     launch_rayleigh_ritz(m, m, m, h->gramA, nullptr, h->lam, h->Cm, h->rrwork, h->status,
                          ST_X_BREAKDOWN, st);
     const unsigned skip = ST_X_BREAKDOWN | ST_RR_BREAKDOWN;
@@ -898,7 +903,7 @@ void pass_body(lobpcg_t* h) {
                         use_p ? b : 0, f64(h->part), (int64_t)h->part_doubles, h->lam, h->gramA, h->gramB, h->status,
                         use_tc(h), st);
     } else {
-        gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr);
+        gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr, true);
     }
     tm.mark(5);
     // step 24: gramA C = gramB C Lambda (P block dropped on device if needed)
@@ -1522,7 +1527,7 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
         const Blocks3 S = blocks(S0, w0, DT_F64, S1, w1, S2, w2, DT_F64, ld);
         const Blocks3 AS = blocks(AS0, w0, DT_F64, AS1, w1, AS2, w2, DT_F64, ld);
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-        gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr);
+        gram(h, S, AS0 ? &AS : nullptr, gramA, gramB, nullptr, true);
         unsigned stw = 0;
         LG_CUDA(cudaMemcpyAsync(&stw, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         LG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1586,7 +1591,7 @@ int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld) {
         cudaStream_t st = h->stream;
         LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
         const Blocks3 SV = blocks(V, b, DT_F64, nullptr, 0, nullptr, 0, DT_F64, ld);
-        gram(h, SV, nullptr, h->gramA, h->Gsmall, nullptr);
+        gram(h, SV, nullptr, h->gramA, h->Gsmall, nullptr, false);
         launch_chol_rinv(b, h->Gsmall, h->Rinv, h->status, ST_W_BREAKDOWN, 0u, st);
         if (ld == h->ld) {
             apply_rinv_f64(h, b, V, h->Rinv, ST_W_BREAKDOWN);
