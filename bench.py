@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 LOBPCG hot path.
 
-A step is one LOBPCG iteration (Algorithm steps 7-33 of the BLOPEX paper, Section 2.2: residual,
+A step is one LOBPCG iteration (Section 2.2 of the BLOPEX paper: residual,
 V-cycle preconditioner, Cholesky orthonormalisation of W and P, stencil SpMV, Gram matrices,
 Rayleigh-Ritz, Ritz update) over the whole block.  Default workload: the paper's 10^8-unknown scale,
 the 7-point Dirichlet Laplacian on a 464^3 interior grid (99,897,344 unknowns), m = 8 eigenpairs,
@@ -66,7 +66,7 @@ def _measured_hbm():
 
 HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 
-# DRAM traffic of the Gram phase (k_oz_exponents + k_gram_oz, steps 17-23) per iteration, from one
+# DRAM traffic of the Gram phase (k_oz_exponents + k_gram_oz, the Gram matrices of the Rayleigh-Ritz basis) per iteration, from one
 # ncu capture on the 128^3 grid (its first-iteration Gram, q = 16 columns: read + write of both
 # launches) scaled by the columns (24 / 16) and the points (464^3 / 128^3) to the workload, keyed
 # by the SHA-256 of k_gram_oz.cu and oz_digits.cuh; a changed source invalidates it (traffic = null).
@@ -151,13 +151,13 @@ class ClockSampler:
 
 
 def gram_flops_per_launch(n, m):
-    """Algorithmic flops of steps 17-23 at b = m: upper triangles of gramA and gramB, q = 3m."""
+    """Algorithmic flops of the Gram matrices of the Rayleigh-Ritz basis at b = m: upper triangles of gramA and gramB, q = 3m."""
     q = 3 * m
     return 2.0 * n * 2 * (q * (q + 1) // 2)
 
 
 def gram_bytes_per_launch(n, m):
-    """Compulsory bytes of steps 17-23 at b = m: the float64 blocks [X W P] and [AX AW AP]
+    """Compulsory bytes of the Gram matrices of the Rayleigh-Ritz basis at b = m: the float64 blocks [X W P] and [AX AW AP]
     (q = 3m columns each) read once, (2m + 4b) * 8 bytes per point."""
     return 2.0 * 3 * m * 8 * n
 
@@ -213,7 +213,7 @@ def cpu_baseline_sample(w, iters=1):
     T = multigrid.VCycle(d["dims"], A.scale, d["levels"])
     X0 = rng.uniform_block(2, A.n, d["m"])
     marks = []
-    # iters + 1 passes; the spacing of the pass ends excludes the setup steps 1-5 and pass 0
+    # iters + 1 passes; the spacing of the pass ends excludes the set-up and pass 0
     # (pass 0 has no P block)
     olob.lobpcg(A, X0, 0.0, iters + 1, T=T, on_pass=lambda k: marks.append(time.perf_counter()))
     per = (marks[-1] - marks[0]) / (len(marks) - 1)
@@ -305,7 +305,7 @@ def run_reference(args, rank, world):
     T = multigrid.VCycle(d["dims"], A.scale, d["levels"])
     X0 = rng.uniform_block(2, A.n, d["m"])
     marks = []
-    # setup (steps 1-5) and pass 0 (no P block) are not steps; then W + K timed passes
+    # the set-up and pass 0 (no P block) are not steps; then W + K timed passes
     olob.lobpcg(A, X0, 0.0, args.warmup + args.steps + 1, T=T, on_pass=lambda k: marks.append(time.perf_counter()))
     timed = marks[args.warmup:]
     per = (timed[-1] - timed[0]) / args.steps
@@ -466,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
                          fp64=ttt_brief(ttt64, out64), mixed=ttt_brief(tttmx, outmx),
                          mixed_speedup=rnd(ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"], 3),
                          max_rel_lambda_diff_mixed_vs_fp64=rnd(lam_diff, 2)),
-        roofline=dict(kernel="Gram phase, steps 17-23: k_oz_exponents + k_gram_oz + k_gram_finalize (float64 "
+        roofline=dict(kernel="Gram phase, the Gram matrices of the Rayleigh-Ritz basis: k_oz_exponents + k_gram_oz + k_gram_finalize (float64 "
                              "Gram by bfloat16 digit products on the tensor cores)", bound="hbm",
                       achieved=achieved, peak=HBM_PEAK_GBS, unit="GB/s", frac=achieved / HBM_PEAK_GBS,
                       traffic=traffic, algorithmic_bytes=gram_bytes_per_launch(n, m), peak_source=HBM_PEAK_SOURCE,

@@ -66,22 +66,22 @@ extern "C" {
 #define LOBPCG_TOL_ABSOLUTE    1   /* ||A x_j - l_j x_j|| <= tol            */
 
 #define LOBPCG_GRAM_EXPLICIT   0   /* all Gram blocks computed, symmetrised */
-#define LOBPCG_GRAM_PAPER      1   /* Lambda / I diagonal blocks (steps 18-22 as printed) */
+#define LOBPCG_GRAM_PAPER      1   /* Lambda / I diagonal blocks (the Gram blocks as printed) */
 
 #define LOBPCG_MAX_M         100   /* largest block size m (float64 form)   */
 #define LOBPCG_MAX_M_MIXED    32   /* largest block size m of the mixed form */
 #define LOBPCG_NPHASES         8
 
 /* Phase indices of lobpcg_info.phase_ms. */
-#define LOBPCG_PH_RESIDUAL     0   /* steps 7-8 (residuals and their norms) */
-#define LOBPCG_PH_PRECOND      1   /* step 9 (the V-cycle) */
-#define LOBPCG_PH_CHOLQR_W     2   /* step 11; mixed form: with the Gram-Schmidt of W against X */
-#define LOBPCG_PH_SPMV         3   /* step 12    */
-#define LOBPCG_PH_CHOLQR_P     4   /* steps 13-16; mixed form: with the Gram-Schmidt of P
+#define LOBPCG_PH_RESIDUAL     0   /* residuals and their norms */
+#define LOBPCG_PH_PRECOND      1   /* the preconditioning (the V-cycle) */
+#define LOBPCG_PH_CHOLQR_W     2   /* the orthonormalisation of W; mixed form: with the Gram-Schmidt of W against X */
+#define LOBPCG_PH_SPMV         3   /* the product A W    */
+#define LOBPCG_PH_CHOLQR_P     4   /* the orthonormalisation of P; mixed form: with the Gram-Schmidt of P
                                       against [X W] and AP_J = A P_J */
-#define LOBPCG_PH_GRAM         5   /* steps 17-23 */
-#define LOBPCG_PH_RR           6   /* step 24    */
-#define LOBPCG_PH_UPDATE       7   /* steps 25-33 */
+#define LOBPCG_PH_GRAM         5   /* the Gram matrices of the Rayleigh-Ritz basis */
+#define LOBPCG_PH_RR           6   /* the Rayleigh-Ritz step    */
+#define LOBPCG_PH_UPDATE       7   /* the Ritz update */
 
 typedef struct lobpcg_handle lobpcg_t;
 
@@ -105,7 +105,7 @@ typedef struct lobpcg_info {
                                 fresh A X once J is empty)                         */
     int32_t reserved;
     double  max_rel_resid;   /* max_j ||A x_j - l_j x_j|| / |l_j|, from A X at exit */
-    double  setup_ms;        /* device time of steps 1-5                           */
+    double  setup_ms;        /* device time of the set-up                           */
     double  solve_ms;        /* device time of the iteration loop                  */
     int64_t kernel_launches; /* kernels this library launched during the call       */
     double  phase_ms[LOBPCG_NPHASES];  /* device time per phase, summed over iterations;
@@ -117,7 +117,7 @@ typedef struct lobpcg_info {
 /* Create a handle on CUDA device `device`.  `stream` is a cudaStream_t (NULL =
  * the legacy default stream); `alloc` may be NULL; `precision` is LOBPCG_FP64
  * or LOBPCG_MIXED.  In the mixed form, once every implicit residual passes the
- * tolerance, a float64 correction sweep (steps 3-4 of the algorithm on the
+ * tolerance, a float64 correction sweep (the initial orthonormalisation and Rayleigh-Ritz step of the algorithm on the
  * current X with a float64 A X) recomputes the Ritz pairs and their residuals;
  * columns that still fail re-enter the iteration (at most 16 sweeps; then the
  * solve returns LOBPCG_NOT_CONVERGED).
@@ -140,7 +140,7 @@ int lobpcg_create(lobpcg_t** h, int device, void* stream,
 int lobpcg_set_operator(lobpcg_t* h, int kind, int nx, int ny, int nz,
                         double scale, const double* kappa_faces);
 
-/* Set the preconditioner T (Algorithm step 9; Section 2.1.1 requires T linear,
+/* Set the preconditioner T (Section 2.2; Section 2.1.1 requires T linear,
  * symmetric, positive definite).  kind = LOBPCG_PRECOND_NONE or _GMG.  For GMG:
  * `levels` >= 1 grid levels, level l+1 having floor(n/2) points per axis;
  * nu_pre = nu_post >= 1 weighted-Jacobi sweeps with weight omega in (0, 1];
@@ -156,7 +156,7 @@ int lobpcg_set_preconditioner(lobpcg_t* h, int kind, int levels, int nu_pre,
 int lobpcg_set_options(lobpcg_t* h, int tol_mode, int gram_mode, int phase_timing);
 
 /* Inner PCG preconditioning (the paper's Section 4.2, "Performance Versus the
- * Number of Inner Iterations"): step 9 applies T = k iterations of
+ * Number of Inner Iterations"): the preconditioning applies T = k iterations of
  * preconditioned conjugate gradients for A E = W_J from E = 0, preconditioned by
  * the preconditioner set with lobpcg_set_preconditioner, each column an
  * independent solve (float64; a column stops early only if p^T A p <= 0 or
@@ -168,7 +168,7 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
 
 /* Engine of the Gram products.
  * Float64 form (and the float64 steps of the mixed form): unless the engine is
- * LOBPCG_ENGINE_SIMT, the Gram matrices of steps 17-23 (and those of
+ * LOBPCG_ENGINE_SIMT, the Gram matrices of the Rayleigh-Ritz basis (and those of
  * lobpcg_op_gram) with at most 48 columns run on the tensor cores by error-free
  * digit products (the Cholesky Grams of single blocks, whose factor decides a
  * breakdown, stay on the float64 pipe): per window of 1024 grid points every
@@ -178,7 +178,7 @@ int lobpcg_set_inner_pcg(lobpcg_t* h, int iters);
  * integers and added in float64 (Ozaki, Ogita and Oishi's error-free splitting;
  * about 2^-48 of the window's largest products, float64 quality for smooth
  * grid functions).  LOBPCG_ENGINE_SIMT keeps the float64 FMA pipe.
- * Mixed form, float32 Gram products (steps 11, 15, 17-23; the double-float
+ * Mixed form, float32 Gram products (the orthonormalisations of W and P and the Gram matrices; the double-float
  * X^T X block is unaffected):
  *   LOBPCG_ENGINE_TENSOR: tcgen05 tensor-core MMAs on 3 x TF32 splits (hi*hi +
  *     hi*lo + lo*hi, about 2^-21 relative per product), float32 accumulation
@@ -213,11 +213,11 @@ int lobpcg_set_gram_engine(lobpcg_t* h, int engine);
  * engine keeps its fixed bounds.  Never returns an error for a valid handle. */
 int lobpcg_set_wait_limit(lobpcg_t* h, int polls);
 
-/* Constraints, the hard locking of the paper's Section 2.3 (Section 2.2, steps 2
- * and 10): Y is an n-by-l block (column j at Y + j * ldy, float64, device memory,
+/* Constraints, the hard locking of the paper's Section 2.3 (the constraint projections of
+ * Section 2.2's algorithm): Y is an n-by-l block (column j at Y + j * ldy, float64, device memory,
  * or host memory if on_host != 0) of l linearly independent columns; it is
- * copied.  The following solves work in the complement of span(Y): step 2
- * projects the initial block, X = X - Y (Y^T Y)^-1 (Y^T X), and step 10 every
+ * copied.  The following solves work in the complement of span(Y): the constraint projection of X
+ * projects the initial block, X = X - Y (Y^T Y)^-1 (Y^T X), and the constraint projection of W every
  * preconditioned residual block, W_J = W_J - Y (Y^T Y)^-1 (Y^T W_J) (B = I), so
  * with the eigenvectors of earlier solves as Y a solve continues the spectrum
  * (the repeated calls the paper recommends for many eigenpairs).  The library
@@ -237,8 +237,8 @@ int lobpcg_set_constraints(lobpcg_t* h, const double* Y, int l, int64_t ldy,
  * m instead of the seeded random block.  Errors: ERR_ARG, ERR_STATE, ERR_CUDA. */
 int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on_host);
 
-/* Solve: steps 1-5, then iterations k = 0..maxit of steps 7-33 until every
- * column satisfies the tolerance (the pass k = maxit performs only steps 7-8).
+/* Solve: the set-up, then iterations k = 0..maxit of the iteration of Section 2.2 until every
+ * column satisfies the tolerance (the pass k = maxit performs only the residuals and the soft-locking test).
  * Soft-locked columns stay in the Rayleigh-Ritz basis (Section 2.3), so a
  * locked column can drift above the tolerance; when J is empty the float64
  * form therefore recomputes every residual from a fresh A X (which replaces
@@ -255,8 +255,8 @@ int lobpcg_set_initial(lobpcg_t* h, const double* X0, int m, int64_t ldx, int on
 int lobpcg_solve(lobpcg_t* h, int m, double tol, int maxit, uint64_t seed,
                  lobpcg_info* out);
 
-/* Step-wise form of lobpcg_solve.  lobpcg_begin performs steps 1-5;
- * lobpcg_iterate then performs up to `steps` passes of steps 7-33 and returns
+/* Step-wise form of lobpcg_solve.  lobpcg_begin performs the set-up;
+ * lobpcg_iterate then performs up to `steps` passes of the iteration of Section 2.2 and returns
  * OK once J is empty (NOT_CONVERGED while columns remain active).  A tol of 0
  * keeps every column active (fixed work per pass).  lobpcg_finish recomputes
  * the residuals from A X (as lobpcg_solve does at exit). */
@@ -298,24 +298,24 @@ int lobpcg_eig_grad_kappa(lobpcg_t* h, const double* w, double* grad_faces);
  * n-by-m block with n = the operator's point count into device X. */
 int lobpcg_op_random_block(lobpcg_t* h, uint64_t seed, int m, double* X, int64_t ldx);
 
-/* Y = A X for `ncols` columns (Algorithm steps 3 and 12): device X, Y, which
+/* Y = A X for `ncols` columns (Section 2.2): device X, Y, which
  * must not overlap. */
 int lobpcg_op_stencil(lobpcg_t* h, int ncols, const double* X, int64_t ldx,
                       double* Y, int64_t ldy);
 
-/* The mixed form's SpMV (Algorithm step 12 on a LOBPCG_MIXED handle): Y = A X
+/* The mixed form's SpMV (Section 2.2, on a LOBPCG_MIXED handle): Y = A X
  * for ncols float32 device columns (n rows, leading dimensions ldx, ldy >= n),
  * float32 arithmetic, each point's six neighbour differences summed before the
  * scaling.  X and Y must not overlap.  ERR_ARG on a LOBPCG_FP64 handle. */
 int lobpcg_op_stencil_f32(lobpcg_t* h, int ncols, const float* X, int64_t ldx,
                           float* Y, int64_t ldy);
 
-/* E = T R for `ncols` columns (Algorithm step 9; T = I copies): device R, E,
+/* E = T R for `ncols` columns (Section 2.2; T = I copies): device R, E,
  * which must not overlap.  Needs a LOBPCG_FP64 handle. */
 int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,
                       double* E, int64_t lde);
 
-/* The mixed form's preconditioner (Algorithm step 9 on a LOBPCG_MIXED handle):
+/* The mixed form's preconditioner (Section 2.2, on a LOBPCG_MIXED handle):
  * E = T R for ncols float32 device columns (n rows, leading dimensions ldr, lde
  * >= n), the V-cycle with float32 arithmetic on every level, float32 storage on
  * the finest and bfloat16 storage on the coarser levels.  ERR_ARG on a
@@ -323,17 +323,17 @@ int lobpcg_op_precond(lobpcg_t* h, int ncols, const double* R, int64_t ldr,
 int lobpcg_op_precond_f32(lobpcg_t* h, int ncols, const float* R, int64_t ldr,
                           float* E, int64_t lde);
 
-/* Column residuals (Algorithm step 7): for t < ncols, j = cols[t] (host array),
+/* Column residuals (Section 2.2): for t < ncols, j = cols[t] (host array),
  * W[:, t] = AX[:, j] - lambda[j] X[:, j] (lambda: device, m values) and
  * norms[t] = ||W[:, t]||_2 (host output).  W may be NULL (norms only). */
 int lobpcg_op_residual(lobpcg_t* h, int ncols, const int* cols, const double* X,
                        const double* AX, int64_t ld, const double* lambda,
                        double* W, int64_t ldw, double* norms);
 
-/* Gram matrices (Algorithm steps 17-23): S = [S0 S1 S2] with widths w0, w1, w2
+/* Gram matrices (Section 2.2): S = [S0 S1 S2] with widths w0, w1, w2
  * (w1, w2 may be 0), each block n rows with leading dimension ld; AS likewise.
  * Writes the q-by-q (q = w0 + w1 + w2) column-major device matrices gramB = S^T S
- * and gramA with the block structure printed in steps 18 / 21: block (I, J) =
+ * and gramA with the block structure printed in Section 2.2: block (I, J) =
  * S_I^T AS_J for I < J, its transpose below the diagonal, and (S_I^T AS_I +
  * AS_I^T S_I)/2 on the diagonal.  AS0 may be NULL (gramA skipped).  The
  * handle's Gram engine applies (tensor-core digit products for q <= 48 unless
@@ -343,7 +343,7 @@ int lobpcg_op_gram(lobpcg_t* h, const double* S0, const double* S1, const double
                    const double* AS0, const double* AS1, const double* AS2,
                    int64_t ld, int w0, int w1, int w2, double* gramA, double* gramB);
 
-/* Float64 Ritz update (Algorithm steps 25-33): with S = [S0 S1 S2] (widths w0,
+/* Float64 Ritz update (Section 2.2): with S = [S0 S1 S2] (widths w0,
  * w1, w2; w1, w2 may be 0; n rows, leading dimension ld >= n) and the
  * q-by-m coefficients C (q = w0 + w1 + w2, column-major, leading dimension q,
  * device), writes Xout = S C and, if Pout != NULL, Pout = S1 C1 + S2 C2 (the
@@ -365,14 +365,14 @@ int lobpcg_op_update(lobpcg_t* h, const double* S0, const double* S1, const doub
                      int64_t ld, int w0, int w1, int w2, int m, const double* C,
                      double* Xout, double* Pout);
 
-/* Cholesky orthonormalisation (Algorithm steps 3, 11, 14-15): G = V^T V,
+/* Cholesky orthonormalisation (Section 2.2): G = V^T V,
  * R = chol(G) computed on the unit-diagonal scaling of G, V <- V R^-1 and, if
  * AV != NULL, AV <- AV R^-1 (in place, device, b columns, leading dimension ld).
  * Returns ERR_BREAKDOWN (buffers untouched) if a pivot of the scaled factor is
  * <= b * 2^-52. */
 int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld);
 
-/* Mixed form, float32 Gram products (Algorithm steps 11 and 13 and the block
+/* Mixed form, float32 Gram products (Section 2.2, and the block
  * Gram-Schmidt projections of W and P that the mixed form adds): with float32
  * device blocks S0 (w0 columns), S1 (w1 columns, may be NULL when w1 = 0) and V
  * (b columns), each n rows with the common leading dimension ld (a multiple of
@@ -384,7 +384,7 @@ int lobpcg_op_cholqr(lobpcg_t* h, int b, double* V, double* AV, int64_t ld);
 int lobpcg_op_gram_f32(lobpcg_t* h, const float* S0, int w0, const float* S1, int w1,
                        const float* V, int b, int64_t ld, double* C, double* G);
 
-/* Mixed form, Gram matrices in residual form (Algorithm steps 17-23): basis
+/* Mixed form, Gram matrices in residual form (Section 2.2): basis
  * S = [X W P] with X given as float32 planes (X = Xh + Xl), W (b columns) and
  * P (bp columns, bp = 0: no P block), and T = [R AW AP] with R = AX - X Lambda
  * (Lambda = diag(lambda), lambda: device, m values); all float32 device blocks,
@@ -400,7 +400,7 @@ int lobpcg_op_gram_residual(lobpcg_t* h, const float* Xh, const float* Xl, const
                             int64_t ld, int m, int b, int bp, const double* lambda,
                             double* gramA, double* gramB);
 
-/* Rayleigh-Ritz (Algorithm step 24) on device matrices: gramA C = gramB C Lambda
+/* Rayleigh-Ritz (Section 2.2) on device matrices: gramA C = gramB C Lambda
  * for q-by-q symmetric gramA, gramB (column-major), the m smallest eigenvalues
  * ascending into device lambda and the gramB-orthonormal eigenvectors into
  * device C (q-by-m, column-major, ld q).  q <= 3 * LOBPCG_MAX_M.  Returns

@@ -20,7 +20,7 @@ Modules
   multigrid  -- the V-cycle preconditioner T (weighted Jacobi, full weighting,
                 trilinear prolongation, exact coarsest solve).
   dense      -- scale-invariant Cholesky (Section 2.2) and the Rayleigh-Ritz
-                generalized eigensolve (Algorithm step 24).
+                generalized eigensolve (Section 2.2).
   lobpcg     -- the block LOBPCG iteration with soft locking (Sections 2.2, 2.3).
 
 Parity status per function is stated in each module header; the V-cycle values

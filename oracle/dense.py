@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 * ``scaled_cholesky`` -- the Cholesky factor used for the orthonormalisation of
-  X, W and P (Algorithm steps 3, 11, 14).  The paper requires the factorisation
+  X, W and P (Section 2.2).  The paper requires the factorisation
   to be invariant to column scaling, or else an explicit normalisation of the
   columns first (Section 2.2, discussion after the algorithm).  Reading used:
   always normalise, i.e. D = diag(G)^-1/2, R' = chol(D G D) (upper),
@@ -11,7 +11,7 @@ TEST INFRASTRUCTURE ONLY (see the package header).
   Numerical breakdown (the paper only warns of it): on the unit-diagonal
   matrix D G D, any pivot (the square of a diagonal entry of R') at or below
   q * eps (q = order, eps = 2^-52) counts as failure.
-* ``rayleigh_ritz`` -- Algorithm step 24: gramA C = gramB C Lambda, the first m
+* ``rayleigh_ritz`` -- the Rayleigh-Ritz step (Section 2.2): gramA C = gramB C Lambda, the first m
   eigenvalues ascending, C gramB-orthonormal.  The library routine
   scipy.linalg.eigh (LAPACK sygvd) is the step.
 

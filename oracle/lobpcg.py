@@ -3,44 +3,44 @@
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 Follows the algorithm of Section 2.2 ("The Detailed Description of the LOBPCG
-Algorithm", steps 1-33) with B = I (so BX = X, BW = W, BP = P and 6m vectors
+Algorithm", the algorithm of Section 2.2) with B = I (so BX = X, BW = W, BP = P and 6m vectors
 are stored, as the paper notes after the algorithm).  Soft locking as in
 Section 2.3: only the active columns J get residuals, preconditioned residuals
 and directions; all m columns of X stay in the Rayleigh-Ritz basis.  A
 constraint block Y (l linearly independent columns; the hard locking of
-Section 2.3) enters in step 2, X = X - Y (Y^T Y)^-1 (Y^T X), and in step 10,
+Section 2.3) enters in the constraint projection of X, X = X - Y (Y^T Y)^-1 (Y^T X), and in the constraint projection of W,
 W_J = W_J - Y (Y^T Y)^-1 (Y^T W_J); without Y both steps are empty.
 
 Readings of points the paper leaves open (each listed in the design notes):
-* convergence test (step 8): column j leaves J when ||A x_j - lambda_j x_j||_2
+* convergence test (the soft-locking test): column j leaves J when ||A x_j - lambda_j x_j||_2
   <= tol * |lambda_j| (``tol_mode="relative"``, default) or <= tol
   (``"absolute"``, the paper's literal wording); J only shrinks while columns
   remain active.
 * final check (``final_check=True``, default): soft-locked columns stay in the
   Rayleigh-Ritz basis (Section 2.3), and inside a cluster of equal Ritz values
-  the step-24 rotation can move part of an active column's error into a locked
+  the Rayleigh-Ritz rotation can move part of an active column's error into a locked
   one after its test.  So when J empties, every residual is recomputed from a
-  fresh A X (which also replaces the implicitly updated AX of steps 32-33);
+  fresh A X (which also replaces the implicitly updated AX of the update of AX);
   columns above the tolerance re-enter J and the iteration continues; the solve
   is converged only when this check passes, so every returned residual meets
   the tolerance (the target the paper's tests state, Section 4.1).
   ``final_check=False`` keeps the printed rule (exit as soon as J is empty).
-* loop bound (step 6, k = 0..MaxIterations): the pass k = maxit performs only
-  steps 7-8; ``iters`` is the k at which J became empty.
-* Gram blocks (steps 18-22): the paper prints only the upper block triangle of
+* loop bound (the iteration loop, k = 0..MaxIterations): the pass k = maxit performs only
+  the residuals and the soft-locking test; ``iters`` is the k at which J became empty.
+* Gram blocks (the Gram blocks): the paper prints only the upper block triangle of
   gramA (the blocks below the diagonal are its transposes); those blocks are
   computed, including the diagonal blocks the paper sets to Lambda and I, which
   are symmetrised (G + G^T)/2 (the explicit variant the paper reports as more
   accurate).  gramB = S^T S.  ``gram="paper"`` sets the diagonal blocks as
   printed in the algorithm.
-* Cholesky (steps 3, 11, 14): scale-invariant via unit-diagonal scaling.
+* Cholesky (the orthonormalisations of X, W and P): scale-invariant via unit-diagonal scaling.
 * breakdown: if chol(P_J^T P_J) or the Rayleigh-Ritz with P fails, the P block
-  is dropped for that iteration (k = 0 form of steps 21-22 and 30-32); if
+  is dropped for that iteration (the form without P at k = 0); if
   chol(X^T X) or chol(W_J^T W_J) fails the solve stops with status "breakdown".
 * at exit every residual is recomputed from A X (not the implicitly updated AX).
 * constraints: (Y^T Y)^-1 is applied through the scale-invariant Cholesky factor
   of Y^T Y; if that factorisation fails (Y not linearly independent) the solve
-  stops with status "breakdown" before step 3.
+  stops with status "breakdown" before the orthonormalisation of X.
 """
 
 from dataclasses import dataclass, field
@@ -75,7 +75,7 @@ class Laplace7:
 
 
 def upper_block_gram(S, AS):
-    """gramA of steps 18 / 21: blocks S_I^T AS_J for I <= J, lower blocks by symmetry,
+    """gramA of the Gram blocks as printed: blocks S_I^T AS_J for I <= J, lower blocks by symmetry,
     diagonal blocks symmetrised."""
     widths = [b.shape[1] for b in S]
     offs = np.concatenate([[0], np.cumsum(widths)])
@@ -92,7 +92,7 @@ def upper_block_gram(S, AS):
 
 
 def constraint_projector(Y):
-    """V -> V - Y (Y^T Y)^-1 (Y^T V) (steps 2 and 10 with B = I), with Y^T Y = R^T R from the
+    """V -> V - Y (Y^T Y)^-1 (Y^T V) (the constraint projections with B = I), with Y^T Y = R^T R from the
     scale-invariant Cholesky; raises Breakdown if Y^T Y is not positive definite."""
     R = scaled_cholesky(Y.T @ Y)
 
@@ -113,7 +113,7 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
     """Smallest m = X0.shape[1] eigenpairs of the operator A, preconditioner T (None = identity),
     in the complement of the constraint block Y ((n, l) array or None).
 
-    ``on_pass(k)`` (optional) is called after steps 9-33 of pass k, for timing only.
+    ``on_pass(k)`` (optional) is called at the end of pass k, for timing only.
     """
     X = np.array(X0, dtype=np.float64, copy=True)
     n, m = X.shape
@@ -127,33 +127,33 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
             constrain = constraint_projector(np.asarray(Y, dtype=np.float64))
         except Breakdown:
             return Result(np.full(m, np.nan), X, 0, "breakdown", np.full(m, np.nan))
-        # Step 2: apply the constraints to X.
+        # constraints: project the initial block
         X = constrain(X)
 
-    # Step 3: orthonormalise X (B = I): R = chol(X^T X), X = X R^-1, AX = A X.
+    # orthonormalise X (B = I): R = chol(X^T X), X = X R^-1, AX = A X
     try:
         R = scaled_cholesky(X.T @ X)
     except Breakdown:
         return Result(np.full(m, np.nan), X, 0, "breakdown", np.full(m, np.nan))
     X = apply_inverse_upper(X, R)
     AX = A(X)
-    # Step 4: initial Ritz vectors from (X^T AX) TMP = TMP Lambda.
+    # initial Ritz vectors from (X^T AX) TMP = TMP Lambda
     lam, TMP = rayleigh_ritz(symmetrize(X.T @ AX), np.eye(m), m)
     X = X @ TMP
     AX = AX @ TMP
-    # Step 5: all columns active.
+    # all columns active
     J = list(range(m))
     P = AP = None
     iters, status = maxit, "not_converged"
 
     for k in range(0, maxit + 1):
-        # Step 7: residuals of the active columns.
+        # residuals of the active columns
         W = AX[:, J] - X[:, J] * lam[J][None, :]
         norms = np.linalg.norm(W, axis=0)
         if not (np.all(np.isfinite(norms)) and np.all(np.isfinite(lam))):
             status, iters = "nonfinite", k
             break
-        # Step 8: soft-lock converged columns; exit when none is left.
+        # soft-lock converged columns; exit when none is left
         keep = [t for t, j in enumerate(J) if not _converged(norms[t], lam[j], tol, tol_mode)]
         if record:
             hist.append(dict(k=k, lam=lam.copy(), J=list(J), norms=norms.copy(),
@@ -174,21 +174,21 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
             break
         if k == maxit:
             break
-        # Step 9: precondition.
+        # precondition
         W = precond(W)
-        # Step 10: apply the constraints to the preconditioned residuals.
+        # constraints: project the preconditioned residuals
         if constrain is not None:
             W = constrain(W)
-        # Step 11: orthonormalise W_J.
+        # orthonormalise W_J
         try:
             R = scaled_cholesky(W.T @ W)
         except Breakdown:
             status, iters = "breakdown", k
             break
         W = apply_inverse_upper(W, R)
-        # Step 12: AW_J = A W_J.
+        # AW_J = A W_J
         AW = A(W)
-        # Steps 13-16: orthonormalise P_J and update AP_J (k > 0).
+        # orthonormalise P_J and update AP_J (k > 0)
         use_p = k > 0
         if use_p:
             PJ, APJ = P[:, J], AP[:, J]
@@ -198,7 +198,7 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
                 APJ = apply_inverse_upper(APJ, R)
             except Breakdown:
                 use_p = False
-        # Steps 17-24: Gram matrices and the Rayleigh-Ritz eigenproblem.
+        # Gram matrices of the basis and the Rayleigh-Ritz eigenproblem
         dropped = False
         while True:
             S = [X, W] + ([PJ] if use_p else [])
@@ -228,7 +228,7 @@ def lobpcg(A, X0, tol, maxit, T=None, tol_mode="relative", gram="explicit", reco
             break
         if record and dropped:
             hist[-1]["dropped_p"] = True
-        # Steps 25-33: Ritz vectors.
+        # Ritz vectors: the update of X and P
         b = len(J)
         CX, CW = C[:m], C[m:m + b]
         P = W @ CW

@@ -63,10 +63,10 @@ struct ColList {
 
 // Device status word bits, written by kernels and read with the residual norms.
 enum StatusBits : unsigned {
-    ST_W_BREAKDOWN = 1u,      // chol(W_J^T W_J) failed (step 11)
+    ST_W_BREAKDOWN = 1u,      // chol(W_J^T W_J) failed (the orthonormalisation of W)
     ST_P_DROPPED = 2u,        // P block dropped this iteration (chol of P or gramB failed)
     ST_RR_BREAKDOWN = 4u,     // gramB not positive definite without P
-    ST_X_BREAKDOWN = 8u,      // chol(X^T X) failed (step 3)
+    ST_X_BREAKDOWN = 8u,      // chol(X^T X) failed (the orthonormalisation of X)
     ST_NONFINITE = 16u,       // non-finite value in a small dense matrix
     ST_TIMEOUT = 32u,         // a bounded wait of a kernel gave up (its results are invalid)
     ST_TIMEOUT_MMA = 64u,     // the tensor-core Gram's wait for its issued MMAs gave up as well
@@ -163,9 +163,9 @@ bool tsmm_oz_fits(int q, int nout);
 bool launch_tsmm_oz(int64_t n, const Blocks3& S, const double* C, int ldc, int nx, int np, int w0p, double* out0,
                     double* out1, int64_t ldout, unsigned* status, unsigned skip, cudaStream_t st,
                     int scale_mode = TZ_SCALE_NONE, const int* sexp = nullptr);
-// gramA (upper block triangle of steps 18 / 21, diagonal blocks symmetrised) and gramB from the
+// gramA (upper block triangle of the Gram blocks as printed, diagonal blocks symmetrised) and gramB from the
 // summed partials.  If paper_lambda != null the X block of gramA is diag(lambda) and the
-// diagonal blocks of gramB are identities (steps 18-22 as printed).
+// diagonal blocks of gramB are identities (the Gram blocks as printed).
 void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, double* gramA,
                           double* gramB, const double* paper_lambda, const Blocks3* widths,
                           cudaStream_t st);
@@ -175,7 +175,7 @@ void launch_gram_finalize(int q, int nparts, const double* part, bool with_a, do
 void launch_apply_rinv(int64_t n, int b, DType t, void* Vin, int64_t ldin, void* Vout,
                        int64_t ldout, const double* Rinv, const unsigned* status,
                        unsigned skip_mask, cudaStream_t st);
-// Ritz update (steps 27-28 / 31-32): Pout = S1 C1 + S2 C2 (type of S1, S2) and
+// Ritz update (the update of X and P): Pout = S1 C1 + S2 C2 (type of S1, S2) and
 // Xout = S0 C0 + Pout (float64), with C (q x m, column-major, ld q, float64) split by rows into
 // C0 (w0), C1 (w1), C2 (w2).  Xout may alias S0 and Pout may alias S2; Pout may be null.
 // Skipped if *status & skip_mask.
@@ -184,7 +184,7 @@ void launch_update(int64_t n, int m, const Blocks3& S, const double* C, double* 
                    void* Pout, int64_t ldout, const unsigned* status, unsigned skip_mask,
                    cudaStream_t st, float* Xh = nullptr, float* Xl = nullptr);
 
-// Coefficients of the constraint projection V - Y (Y^T V) (steps 2 and 10 with an orthonormal
+// Coefficients of the constraint projection V - Y (Y^T V) (the constraint projections with an orthonormal
 // Y): C ((b + k) x b) = [I; -(Y^T V)] from the Gram matrix G of [V Y] ((b + k) x (b + k)), for
 // launch_update over the blocks [V Y].
 void launch_proj_coef(int b, int k, const double* G, double* C, cudaStream_t st);

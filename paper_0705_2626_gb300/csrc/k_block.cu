@@ -1,10 +1,10 @@
 // Tall-skinny block kernels of one LOBPCG iteration (B = I):
 //   random initial block (Algorithm input X, SplitMix64 counter generator),
-//   residuals and their norms (steps 7-8),
-//   Gram matrices [X W_J P_J]^T [AX AW_J AP_J] and [X W_J P_J]^T [X W_J P_J] (steps 17-23,
-//   and the Cholesky Gram matrices of steps 3, 11, 14),
-//   multiplication by the inverse Cholesky factor (steps 3, 11, 14-15),
-//   the Ritz update of P, AP, X, AX (steps 25-33).
+//   residuals and their norms (Section 2.2),
+//   Gram matrices [X W_J P_J]^T [AX AW_J AP_J] and [X W_J P_J]^T [X W_J P_J] (the Gram matrices of the Rayleigh-Ritz basis,
+//   and the Cholesky Gram matrices of the orthonormalisations of X, W and P),
+//   multiplication by the inverse Cholesky factor (the orthonormalisations of X, W and P),
+//   the Ritz update of P, AP, X, AX (the Ritz update).
 // Blocks are float64 in the FP64 form; in the mixed form X and AX stay float64 and the W / P
 // family is float32 (products in float32, sums compensated).  Reductions over the n grid points
 // are deterministic: per-thread-block partial sums land in scratch memory and are added in a
@@ -112,7 +112,7 @@ __host__ __device__ inline int block_of(const Blocks3& B, int c) {
 }
 
 // Output tile (ti, tj) of S^T AS is needed when it holds an entry (i, j) with
-// block(i) <= block(j): the upper block triangle of steps 18 / 21, diagonal blocks in full.
+// block(i) <= block(j): the upper block triangle of the Gram blocks as printed, diagonal blocks in full.
 // First tile column of the needed A tiles in tile row ti: the tile holding the first column of
 // the block of column ti * kTM (block(j) >= block(i) from there on).
 __host__ __device__ inline int a_tile_first(const Blocks3& B, int ti) {

@@ -1,6 +1,6 @@
 // Small dense kernels of one LOBPCG iteration, in float64, each on one thread block:
 //  * k_chol_rinv: the scale-invariant Cholesky factor of a b x b Gram matrix and its inverse
-//    (Algorithm steps 3, 11, 14; the paper requires invariance to column scaling, Section 2.2,
+//    (Section 2.2; the paper requires invariance to column scaling, Section 2.2,
 //    so the factor is computed on D G D with D = diag(G)^-1/2 and R = R' D^-1).
 //  (the Rayleigh-Ritz step lives in k_rr.cu)
 // Breakdown rule of both: a pivot of the unit-diagonal matrix at or below order * 2^-52 fails.

@@ -1,4 +1,4 @@
-// Tall-skinny Gram products of the mixed form (Algorithm steps 11, 15 and 17-23 on float32
+// Tall-skinny Gram products of the mixed form (Section 2.2, on float32
 // data), staged into shared memory by the Tensor Memory Accelerator.
 //
 // Every product here is S_i^T S_j over n grid points for float32 column blocks with a common

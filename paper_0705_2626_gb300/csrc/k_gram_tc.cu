@@ -1,4 +1,4 @@
-// Tensor-core form of the float32 Gram products of the mixed form (Algorithm steps 11, 15 and
+// Tensor-core form of the float32 Gram products of the mixed form (Section 2.2, and
 // 17-23): tcgen05 MMAs with operands staged by TMA in shared memory and accumulators in tensor
 // memory (TMEM).
 //

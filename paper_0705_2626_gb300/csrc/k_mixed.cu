@@ -5,8 +5,8 @@
 // significant bits, 2^-48 relative -- well below what the 1e-8 residual tolerance needs), so that
 // the two X-side operations of every iteration run on the float32 units instead of GB300's
 // float64 units (1/64 of the float32 rate):
-//   * the Ritz update (Algorithm steps 25-33; k_tsmm.cu);
-//   * the residual (step 7) R = A X - X Lambda from the planes, with the 7-point stencil and the
+//   * the Ritz update (Section 2.2; k_tsmm.cu);
+//   * the residual (the residuals) R = A X - X Lambda from the planes, with the 7-point stencil and the
 //     Lambda X product in double-float and R rounded to float32 at the end, plus the squared
 //     column norms.
 // Double-float conventions: a product a*b of float32 values is made exact as (p, e) with

@@ -1,4 +1,4 @@
-// Rayleigh-Ritz step (Algorithm step 24): gramA C = gramB C Lambda, the m smallest eigenpairs,
+// Rayleigh-Ritz step (Section 2.2): gramA C = gramB C Lambda, the m smallest eigenpairs,
 // C gramB-orthonormal.  GB300 runs float64 at 1/64 of the float32 rate, and one thread block
 // alone would spend most of an iteration on the O(q^3) float64 work of a Jacobi eigensolver, so
 // the work is split:
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024)
     if (*status & skip) return;
     RRWork w(work, q);
     // L and its inverse, row-major: in shared memory (leading dimension q + 1) while they fit,
-    // else in the work area's R and E (leading dimension q; both are free until step 4)
+    // else in the work area's R and E (leading dimension q; both are free until the initial Rayleigh-Ritz step)
     const bool in_smem = rr_chol_smem(q) != 0;
     const int ld = in_smem ? q + 1 : q;
     double* Lsm = in_smem ? sm : w.R;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(1024)
     RRWork w(work, q);
     const int nq = nq_of(w);
     // A and V in shared memory while they fit, else (float32, leading dimension nq) in the work
-    // area's MV, which is free until step 4
+    // area's MV, which is free until the initial Rayleigh-Ritz step
     const bool in_smem = rr_jacobi_smem(q) != 0;
     const int ld = in_smem ? nq + 1 : nq;
     float* A = in_smem ? smf : reinterpret_cast<float*>(w.MV);

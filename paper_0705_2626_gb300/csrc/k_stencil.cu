@@ -1,5 +1,5 @@
-// Stencil-family kernels: the block 7-point SpMV (Algorithm steps 3 and 12) and the
-// kernels of the multigrid V-cycle that serves as the preconditioner T (step 9).
+// Stencil-family kernels: the block 7-point SpMV (Section 2.2) and the
+// kernels of the multigrid V-cycle that serves as the preconditioner T (the preconditioning).
 //
 // All of them are one generic structured sweep
 //     y = a*x + b*(sum of the six neighbours of x) [+ c*z]          (zero outside the grid)

@@ -9,11 +9,11 @@
 // float4 stores.  Because every input of a tile is in shared memory before any output of that
 // tile is written, the products can run in place.  Four forms:
 //   PROJECT   V <- V - [L0 L1] C          (block Gram-Schmidt of the mixed form)
-//   APPLY     V <- V Rinv, Rinv upper      (Cholesky orthonormalisation, steps 11 / 15)
+//   APPLY     V <- V Rinv, Rinv upper      (Cholesky orthonormalisation, the orthonormalisations of W and P)
 //   GENERAL   V <- [L0 L1 V] K             (the last Gram-Schmidt pass and the Cholesky step in
 //                                           one pass: K = [-C Rinv; Rinv])
 //   UPDATE    P <- W C_W + P C_P (float32), X <- X C_X + P in double-float, X as hi / lo planes
-//             (Ritz update, steps 25-33)
+//             (Ritz update, the Ritz update)
 #include <algorithm>
 #include <atomic>
 

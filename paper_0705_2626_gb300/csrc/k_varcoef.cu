@@ -37,7 +37,7 @@ struct FaceIdx {
     __host__ __device__ int64_t z(int i, int j, int f) const { return oz + i + (int64_t)nx * (j + (int64_t)ny * f); }
 };
 
-// mode 0: y = scale (D x - N x)                        (SpMV, steps 3 and 12)
+// mode 0: y = scale (D x - N x)                        (SpMV, the products A X and A W)
 // mode 1: y = (1 - w) x + w (z / (scale D) + N x / D)  (weighted Jacobi on e = x with r = z)
 // mode 2: y = z - scale (D x - N x)                    (residual r - A e)
 // mode 3: y = w z / (scale D)                          (first Jacobi sweep from e = 0)

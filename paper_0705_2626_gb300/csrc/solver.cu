@@ -2,7 +2,7 @@
 //
 // One handle = one operator (7-point Laplacian on an nx x ny x nz grid), one preconditioner
 // (V-cycle hierarchy or identity) and the workspace of a block of m vectors.  The iteration
-// follows Section 2.2 of the BLOPEX paper (steps 1-33) with B = I (6m stored vectors), no
+// follows Section 2.2 of the BLOPEX paper (the algorithm of Section 2.2) with B = I (6m stored vectors), no
 // constraints and the soft locking of Section 2.3.  Every step runs in this library's kernels;
 // the host only keeps the active index set J, which needs the b residual norms of each
 // iteration (one device-to-host copy per iteration, together with a status word that the small
@@ -11,7 +11,7 @@
 // Two forms.  LOBPCG_FP64: every block and every operation in float64.  LOBPCG_MIXED: X, AX and
 // all small matrices in float64; W, AW, P, AP, the V-cycle's finest level in float32 and its
 // coarser levels stored in bfloat16; the Gram products in float32 with compensated sums.  When
-// every implicit residual passes, a float64 correction sweep (steps 3-4 applied to the current X
+// every implicit residual passes, a float64 correction sweep (the initial orthonormalisation and Rayleigh-Ritz step applied to the current X
 // with a fresh float64 A X) recomputes the Ritz pairs and their residuals; columns that fail
 // re-enter the loop.
 #include <algorithm>
@@ -77,7 +77,7 @@ struct lobpcg_handle {
     // options
     int tol_mode = LOBPCG_TOL_RELATIVE, gram_mode = LOBPCG_GRAM_EXPLICIT, phase_timing = 0;
     int gram_engine = LOBPCG_ENGINE_AUTO;       // float32 Grams of the mixed form
-    int inner_pcg = 0;                          // inner PCG iterations of step 9 (0: V-cycle directly)
+    int inner_pcg = 0;                          // inner PCG iterations of the preconditioning (0: V-cycle directly)
     int wait_limit = -1;                        // poll limit of the TMA stage waits (< 0: default)
     Buf pcg_small;                              // inner PCG scalars: rz, rz', pAp (b each), active flags
 
@@ -102,7 +102,7 @@ struct lobpcg_handle {
     Buf X0;
     int X0_m = 0;
 
-    // constraint block Y (steps 2 and 10): an orthonormal basis Q of span(Y), float64, and its
+    // constraint block Y (the constraint projections): an orthonormal basis Q of span(Y), float64, and its
     // float32 copy for the mixed form; orthonormalised at the first solve after it is set
     Buf Yq, Yq32;
     int ncon = 0;
@@ -382,7 +382,7 @@ void precond(lobpcg_t* h, int b, DType t, const void* r, int64_t ldr, void* e, i
     vcycle(h, 0, b, t, r, ldr, e, lde, tmp, ldt);
 }
 
-// Step 9 with an inner PCG solve (Section 4.2): E = T_k(R) = the k-th iterate (k = inner_pcg) of
+// The preconditioning with an inner PCG solve (Section 4.2): E = T_k(R) = the k-th iterate (k = inner_pcg) of
 // PCG for A E = R from E = 0, preconditioned by the V-cycle, columns independent; float64, all
 // blocks with the workspace's leading dimension.  R is overwritten (it becomes the PCG residual);
 // Z, P, AP and tmp are scratch blocks of b columns.
@@ -442,9 +442,9 @@ bool tsmm_f64(lobpcg_t* h, const Blocks3& S, const double* C, int ldc, int nx, i
                           sexp);
 }
 
-// Float64 Ritz update (steps 25-33): Pout = S_1 C_1 + S_2 C_2 (rows >= w0 of C = h->Cm) if Pout is
+// Float64 Ritz update (the Ritz update): Pout = S_1 C_1 + S_2 C_2 (rows >= w0 of C = h->Cm) if Pout is
 // not null, and Xout = S C (outputs with the leading dimension of S); in place over S_0 / S_2
-// allowed.  side: 0 for S = [X W P], 1 for [AX AW AP]; when the last Gram (steps 17-23) ran on the
+// allowed.  side: 0 for S = [X W P], 1 for [AX AW AP]; when the last Gram (the Gram matrices of the Rayleigh-Ritz basis) ran on the
 // tensor cores over this basis, its column exponents equilibrate the columns (AX, AW and AP may
 // differ in scale by orders of magnitude).
 void update_f64(lobpcg_t* h, int m, const Blocks3& S, double* Xout, double* Pout, unsigned skip, int side) {
@@ -465,7 +465,7 @@ void apply_rinv_f64(lobpcg_t* h, int b, double* V, const double* Rinv, unsigned 
 }
 
 // Gram matrices of S (and S^T AS).  tensor: the tensor-core digit products may serve (the Grams
-// of steps 17-23); the Cholesky Grams of single blocks pass false and stay on the float64 pipe:
+// of the Gram matrices of the Rayleigh-Ritz basis); the Cholesky Grams of single blocks pass false and stay on the float64 pipe:
 // their factor decides breakdown (R9) and is inverted, and the tensor Grams' errors, relative to
 // each window's largest entries, are coarser than those of float64 sums on the nearly dependent
 // blocks near convergence (a 128^3, m = 48 solve broke down on W_J with them, converged without).
@@ -513,7 +513,7 @@ void project_normalize(lobpcg_t* h, int b, void* V, const void* W, unsigned fail
     const float* Wf = static_cast<const float*>(W);
     float* Vf = static_cast<float*>(V);
     cudaStream_t st = h->stream;
-    // pass 1: V <- V - L (L^T V); the coefficients in gramB, which is free until steps 17-23
+    // pass 1: V <- V - L (L^T V); the coefficients in gramB, which is free until the Gram matrices of the Rayleigh-Ritz basis
     launch_gram32_cross(n, h->ld, Xh, m, Wf, wb, Vf, b, h->gramB, nullptr, f64(h->part), (int64_t)h->part_doubles,
                         h->status, use_tc(h), st);
     launch_project32(n, b, Vf, Xh, m, Wf, wb, h->ld, h->gramB, m + wb, h->status, st);
@@ -527,7 +527,7 @@ void project_normalize(lobpcg_t* h, int b, void* V, const void* W, unsigned fail
     launch_combine32(n, b, Vf, Xh, m, Wf, wb, h->ld, h->gramA, m + wb + b, h->status, skip, h->status, st);
 }
 
-// V <- V Rinv (steps 11 and 15), in place; skipped on the device if *status & skip.
+// V <- V Rinv (the orthonormalisations of W and P), in place; skipped on the device if *status & skip.
 void apply_rinv(lobpcg_t* h, int b, DType t, void* V, unsigned skip) {
     if (t == DT_F32)
         launch_apply32(h->g.n(), b, static_cast<float*>(V), h->ld, h->Rinv, h->status, skip, h->status, h->stream);
@@ -535,7 +535,7 @@ void apply_rinv(lobpcg_t* h, int b, DType t, void* V, unsigned skip) {
         apply_rinv_f64(h, b, static_cast<double*>(V), h->Rinv, skip);
 }
 
-// G = V^T V for the Cholesky orthonormalisation of a W / P block (steps 11 and 13).
+// G = V^T V for the Cholesky orthonormalisation of a W / P block (the orthonormalisations of W and P).
 void block_gram(lobpcg_t* h, int b, DType t, const void* V, double* G) {
     if (t == DT_F32) {
         launch_gram32_cross(h->g.n(), h->ld, nullptr, 0, nullptr, 0, static_cast<const float*>(V), b, nullptr, G,
@@ -564,7 +564,7 @@ void events_create(lobpcg_t* h) {
 // ------------------------------------------------------------------ the iteration
 void residual_into_W(lobpcg_t* h) {
     h->norms_fp64 = true;
-    // step 7: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]] and the norms (to the host).  The
+    // the residuals: W[:, t] = AX[:, J[t]] - lambda[J[t]] X[:, J[t]] and the norms (to the host).  The
     // mixed form computes the residual R of all m columns (its Gram uses R for every column).
     const int64_t n = h->g.n();
     const bool mixed = h->precision == LOBPCG_MIXED;
@@ -581,7 +581,7 @@ void residual_into_W(lobpcg_t* h) {
     launch_norms_finalize(cols.n, residual_chunks(n), f64(h->part), h->norms, h->stream);
 }
 
-// Mixed form, step 7 from the double-float planes of X: R = A X - X Lambda for all m columns.
+// Mixed form, the residuals from the double-float planes of X: R = A X - X Lambda for all m columns.
 void residual_from_planes(lobpcg_t* h) {
     const int m = h->m;
     h->norms_fp64 = false;
@@ -616,12 +616,12 @@ unsigned fetch_small(lobpcg_t* h) {
     return st;
 }
 
-// Steps 3-4 on the current X, all in float64: X = X R^-1 with R = chol(X^T X), AX = A X,
-// (X^T AX) TMP = TMP Lambda, X = X TMP, AX = AX TMP; then step 7 for all m columns.
+// The initial orthonormalisation and Rayleigh-Ritz step on the current X, all in float64: X = X R^-1 with R = chol(X^T X), AX = A X,
+// (X^T AX) TMP = TMP Lambda, X = X TMP, AX = AX TMP; then the residuals for all m columns.
 // This is the setup of the algorithm and, in the mixed form, the float64 correction sweep.
-// ------------------------------------------------------------------ constraints (steps 2 and 10)
+// ------------------------------------------------------------------ constraints (the constraint projections)
 // The handle keeps an orthonormal basis Q of span(Y); with it the projector
-// Y (Y^T Y)^-1 Y^T of steps 2 and 10 (B = I) is Q Q^T, applied chunk by chunk (chunks of Q sized
+// Y (Y^T Y)^-1 Y^T of the constraint projections (B = I) is Q Q^T, applied chunk by chunk (chunks of Q sized
 // so that [V Q_c] fits the Gram scratch of the workspace: b + k <= 3 wm).
 void free_constraints(lobpcg_t* h) {
     dfree(h, h->Yq);
@@ -638,8 +638,8 @@ void project_chunk64(lobpcg_t* h, int b, double* V, const double* Qc, int k) {
     launch_update(h->g.n(), b, S, h->gramA, V, nullptr, h->ld, nullptr, 0u, h->stream);
 }
 
-// Steps 2 / 10: V <- V - Y (Y^T Y)^-1 Y^T V for the b columns of V (type t).  Float64: one pass
-// over the chunks of Q.  Float32 (mixed form, step 10 on W_J): two passes of block Gram-Schmidt
+// The constraint projections: V <- V - Y (Y^T Y)^-1 Y^T V for the b columns of V (type t).  Float64: one pass
+// over the chunks of Q.  Float32 (mixed form, the constraint projection of W on W_J): two passes of block Gram-Schmidt
 // against the float32 copy of Q (the float32 roundings of one pass leave ~1e-7 of span(Y)).
 void apply_constraints(lobpcg_t* h, int b, DType t, void* V) {
     if (h->ncon == 0 || b == 0) return;
@@ -726,7 +726,7 @@ void check_setup_status(lobpcg_t* h, unsigned stw) {
     if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite entry in the block X");
     if (stw & (ST_X_BREAKDOWN | ST_RR_BREAKDOWN))
-        throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (step 3)");
+        throw Error(LOBPCG_ERR_BREAKDOWN, "X^T X is not numerically positive definite (the orthonormalisation of X)");
     for (double v : h->lam_h)
         if (!std::isfinite(v)) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value");
 }
@@ -758,10 +758,10 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     // input block
     if (h->X0.p && h->X0_m == m) copy_cols(h, m, n, DT_F64, h->X0.p, n, h->X.p, h->ld);
     else launch_random_block(seed, n, m, f64(h->X), h->ld, st);
-    // step 2: apply the constraints to X
+    // the constraint projection of X: apply the constraints to X
     prepare_constraints(h);
     apply_constraints(h, m, DT_F64, h->X.p);
-    // steps 3-5 and step 7 of k = 0
+    // the set-up and the residuals of k = 0
     orthonormalize_and_rr(h);
     LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 1], st));
     const unsigned stw = fetch_small(h);
@@ -774,7 +774,7 @@ void begin(lobpcg_t* h, int m, double tol, uint64_t seed) {
     h->state = 1;
 }
 
-// Steps 7-8 with the norms of the last residual pass: shrink J.  Returns true if J is empty.
+// The residuals and the soft-locking test with the norms of the last residual pass: shrink J.  Returns true if J is empty.
 bool check_and_lock(lobpcg_t* h) {
     if (!h->pending_check) return h->J.empty();
     h->pending_check = false;
@@ -817,7 +817,7 @@ bool check_and_lock(lobpcg_t* h) {
     return h->J.empty();
 }
 
-// Steps 9-33 for the current J, then step 7 of the next pass.
+// The iteration from the preconditioning on for the current J, then the residuals of the next pass.
 void pass_body(lobpcg_t* h) {
     const int64_t n = h->g.n();
     const int m = h->m, b = (int)h->J.size();
@@ -826,7 +826,7 @@ void pass_body(lobpcg_t* h) {
     cudaStream_t st = h->stream;
     PhaseTimer tm(h);
     tm.mark(0);
-    // step 9: W_J = T W_J (output in E0, then the buffers swap roles).  The mixed form keeps the
+    // the preconditioning: W_J = T W_J (output in E0, then the buffers swap roles).  The mixed form keeps the
     // residuals of all columns in R and preconditions R[:, J].
     const bool mixed = h->precision == LOBPCG_MIXED;
     const void* rin = h->W.p;
@@ -845,9 +845,9 @@ void pass_body(lobpcg_t* h) {
         precond(h, b, tw, rin, ld, h->E0.p, ld, h->T0.p, ld);
     std::swap(h->W, h->E0);
     tm.mark(1);
-    // step 10: apply the constraints to the preconditioned residuals
+    // the constraint projection of W: apply the constraints to the preconditioned residuals
     apply_constraints(h, b, tw, h->W.p);
-    // step 11: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form first projects W_J against X)
+    // the orthonormalisation of W: W_J = W_J R^-1, R = chol(W_J^T W_J) (the mixed form first projects W_J against X)
     if (mixed) {
         project_normalize(h, b, h->W.p, nullptr, ST_W_BREAKDOWN, 0u);
     } else {
@@ -856,10 +856,10 @@ void pass_body(lobpcg_t* h) {
         apply_rinv(h, b, tw, h->W.p, ST_W_BREAKDOWN);
     }
     tm.mark(2);
-    // step 12: AW_J = A W_J
+    // the product A W: AW_J = A W_J
     spmv(h, b, tw, h->W.p, ld, h->AW.p, ld);
     tm.mark(3);
-    // steps 13-16: P_J = P_J R^-1, AP_J = AP_J R^-1 with R = chol(P_J^T P_J)
+    // the orthonormalisation of P: P_J = P_J R^-1, AP_J = AP_J R^-1 with R = chol(P_J^T P_J)
     const bool use_p = h->k > 0;
     void* Pj = h->P.p;
     void* APj = h->AP.p;
@@ -893,7 +893,7 @@ void pass_body(lobpcg_t* h) {
         }
     }
     tm.mark(4);
-    // steps 17-23: Gram matrices of the basis [X W_J P_J]
+    // the Gram matrices of the Rayleigh-Ritz basis: Gram matrices of the basis [X W_J P_J]
     const Blocks3 S = blocks(h->X.p, m, DT_F64, h->W.p, b, Pj, use_p ? b : 0, tw, ld);
     const Blocks3 AS = blocks(h->AX.p, m, DT_F64, h->AW.p, b, APj, use_p ? b : 0, tw, ld);
     const int q = S.q();
@@ -906,11 +906,11 @@ void pass_body(lobpcg_t* h) {
         gram(h, S, &AS, h->gramA, h->gramB, h->gram_mode == LOBPCG_GRAM_PAPER ? h->lam : nullptr, true);
     }
     tm.mark(5);
-    // step 24: gramA C = gramB C Lambda (P block dropped on device if needed)
+    // the Rayleigh-Ritz step: gramA C = gramB C Lambda (P block dropped on device if needed)
     launch_rayleigh_ritz(q, m + b, m, h->gramA, h->gramB, h->lam, h->Cm, h->rrwork, h->status,
                          ST_W_BREAKDOWN, st);
     tm.mark(6);
-    // steps 25-33: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
+    // the Ritz update: P = W_J C_W + P_J C_P, X = X C_X + P (and the A-side)
     const unsigned skip = ST_W_BREAKDOWN | ST_RR_BREAKDOWN;
     if (mixed) {
         // Mixed form: X as double-float planes; no AX update -- the next residual applies A to X
@@ -924,7 +924,7 @@ void pass_body(lobpcg_t* h) {
         update_f64(h, m, AS, f64(h->AX), f64(h->AP), skip, 1);
     }
     tm.mark(7);
-    // step 7 of the next pass
+    // the residuals of the next pass
     if (mixed) residual_from_planes(h);
     else residual_into_W(h);
     if (tm.on) LG_CUDA(cudaEventRecord(h->ev[LOBPCG_NPHASES + 2], st));
@@ -944,9 +944,9 @@ void pass_body(lobpcg_t* h) {
     if (stw & ST_TIMEOUT) throw Error(LOBPCG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (stw & ST_P_DROPPED) ++h->p_dropped;
     if (stw & ST_W_BREAKDOWN)
-        throw Error(LOBPCG_ERR_BREAKDOWN, "W_J^T W_J is not numerically positive definite (step 11)");
+        throw Error(LOBPCG_ERR_BREAKDOWN, "W_J^T W_J is not numerically positive definite (the orthonormalisation of W)");
     if (stw & ST_RR_BREAKDOWN)
-        throw Error(LOBPCG_ERR_BREAKDOWN, "gramB is not numerically positive definite (step 24)");
+        throw Error(LOBPCG_ERR_BREAKDOWN, "gramB is not numerically positive definite (the Rayleigh-Ritz step)");
     if (stw & ST_NONFINITE) throw Error(LOBPCG_ERR_NONFINITE, "non-finite Ritz value");
     h->k += 1;
     h->pending_check = true;
@@ -957,7 +957,7 @@ void pass_body(lobpcg_t* h) {
 void fp64_correction(lobpcg_t* h) {
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     sync_x_from_planes(h);
-    apply_constraints(h, h->m, DT_F64, h->X.p);     // step 2 in float64 before steps 3-4
+    apply_constraints(h, h->m, DT_F64, h->X.p);     // the constraint projection of X in float64 before the initial orthonormalisation and Rayleigh-Ritz step
     orthonormalize_and_rr(h);
     const unsigned stw = fetch_small(h);
     LG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
@@ -967,7 +967,7 @@ void fp64_correction(lobpcg_t* h) {
 }
 
 // Float64 form, once J is empty: the final check.  Soft-locked columns stay in the Rayleigh-Ritz
-// basis (Section 2.3) and, inside a cluster of equal Ritz values, the step-24 rotation can lift a
+// basis (Section 2.3) and, inside a cluster of equal Ritz values, the Rayleigh-Ritz rotation can lift a
 // locked column above the tolerance after its test.  So A X is recomputed (it replaces the
 // implicitly updated AX), the residuals of all m columns are tested, and the failing ones re-enter
 // J (check_and_lock compacts W to them).  The solve converges only when this check passes.
@@ -1322,7 +1322,7 @@ int lobpcg_iterate(lobpcg_t* h, int steps, lobpcg_info* out) {
         LG_REQUIRE(h->state == 1, LOBPCG_ERR_STATE, "call lobpcg_begin first");
         LG_REQUIRE(steps >= 0, LOBPCG_ERR_ARG, "steps must be >= 0");
         int r = LOBPCG_NOT_CONVERGED;
-        // `steps` passes of steps 7-33, then the check of the pass after them
+        // `steps` passes of the iteration of Section 2.2, then the check of the pass after them
         r = run_passes(h, steps);
         return r;
     });

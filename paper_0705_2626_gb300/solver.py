@@ -141,11 +141,11 @@ class Solver:
                                        on_host), self.h)
 
     def set_inner_pcg(self, iters):
-        """Step 9 as `iters` inner PCG iterations preconditioned by the V-cycle (0: V-cycle directly)."""
+        """The preconditioning as `iters` inner PCG iterations preconditioned by the V-cycle (0: V-cycle directly)."""
         _check(capi.lobpcg_set_inner_pcg(self.h, int(iters)), self.h)
 
     def set_constraints(self, Y):
-        """Constraint block (hard locking, steps 2 and 10): Y an (l, n) float64 tensor (host or
+        """Constraint block (hard locking, the constraint projections): Y an (l, n) float64 tensor (host or
         device), row j = column j; None or l = 0 removes the constraints."""
         if Y is None:
             _check(capi.lobpcg_set_constraints(self.h, None, 0, self.n, 0), self.h)

@@ -1,4 +1,4 @@
-"""Constraints / hard locking (Section 2.2 steps 2 and 10, Section 2.3) on the GPU.
+"""Constraints / hard locking (Section 2.2 the constraint projections, Section 2.3) on the GPU.
 
 Parity with the oracle (oracle/lobpcg.py with Y) on the same seeded start: eigenvalues 1e-10
 relative, iteration counts within 10 %, eigenvectors within the residual / gap bound, and X

@@ -3,7 +3,7 @@
 
 Inputs are float32 blocks; the expected values are float64 products of the same float32 values
 (the plain definitions S^T V, V^T V) and, for the residual form, the oracle's Gram matrices of
-steps 17-23 (upper block triangle, symmetrised diagonal blocks) of the basis [X W P] with
+the Gram matrices of the Rayleigh-Ritz basis (upper block triangle, symmetrised diagonal blocks) of the basis [X W P] with
 X = Xh + Xl.  The residual form equals them in exact arithmetic; the bounds allow the float32
 rounding of the inputs R, AW, AP and the arithmetic of the engine, relative to |s_i| |t_j|:
   SIMT: float32 products, compensated sums: 1e-6;

@@ -186,7 +186,7 @@ def test_gram_matches_definition(dims, widths):
     offs = np.concatenate([[0], np.cumsum(widths)])
     Sb = [S[:, offs[i]:offs[i + 1]] for i in range(3) if widths[i]]
     ASb = [AS[:, offs[i]:offs[i + 1]] for i in range(3) if widths[i]]
-    wantA = olob.upper_block_gram(Sb, ASb)      # steps 18 / 21: upper block triangle
+    wantA = olob.upper_block_gram(Sb, ASb)      # the Gram blocks as printed: upper block triangle
     wantB = S.T @ S
     nrmS, nrmA = np.linalg.norm(S, axis=0), np.linalg.norm(AS, axis=0)
     boundA = 2 * n * EPS * (np.outer(nrmS, nrmA) + np.outer(nrmA, nrmS)) / 2

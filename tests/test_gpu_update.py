@@ -1,4 +1,4 @@
-"""Float64 Ritz update (Algorithm steps 25-33) through the C ABI, against its definition
+"""Float64 Ritz update (Section 2.2) through the C ABI, against its definition
 X = [S0 S1 S2] C and P = [S1 S2] C(w0:, :).
 
 With the default engine, bases of at most 32 columns and at most 28 outputs run on the tensor

@@ -99,7 +99,7 @@ def test_varcoef_solve_and_gradient_match_oracle():
 
 
 def test_gradient_directional_fd_box5():
-    """Central difference (step 1e-6) along a dense random direction over all 1,493,504 faces."""
+    """Central difference (the initial blocke-6) along a dense random direction over all 1,493,504 faces."""
     dims, m = BOX5, 6
     kappa = fields.random_kappa(dims, seed=3, length=8.0, std=1.0)
     assert kappa.size == 1493504

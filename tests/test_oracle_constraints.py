@@ -1,4 +1,4 @@
-"""Pins of the oracle's constraint steps (Section 2.2 steps 2 and 10, the hard locking of
+"""Pins of the oracle's constraint steps (Section 2.2 the constraint projections, the hard locking of
 Section 2.3) against brute force.
 
 The ground truth is a dense eigendecomposition of the 7-point Laplacian assembled here as a
@@ -58,9 +58,9 @@ def test_constrained_iteration_returns_the_next_eigenpairs(truth):
         assert c > 1 - 1e-12
 
 
-def test_step_10_keeps_a_mixing_preconditioner_out_of_span_y(truth):
+def test_constraint_projection_keeps_a_mixing_preconditioner_out_of_span_y(truth):
     """A diagonal preconditioner that does not commute with A puts components of span(Y) into
-    T R; only step 10 keeps them out (without it the iteration drifts to the locked pairs)."""
+    T R; only the constraint projection of W keeps them out (without it the iteration drifts to the locked pairs)."""
     A, mu, V = truth
     l, m = 5, 4
     Y = V[:, :l]

@@ -152,7 +152,7 @@ def test_soft_locked_pairs_keep_improving():
 
 
 def test_paper_gram_variant_agrees_with_explicit():
-    """Steps 18-22 as printed (Lambda and I blocks) vs the explicit Gram blocks."""
+    """The Gram blocks as printed (Lambda and I blocks) vs the explicit Gram blocks."""
     dims = (20, 20, 20)
     A = L.Laplace7(dims)
     T = multigrid.VCycle(dims, A.scale, 3)
@@ -205,7 +205,7 @@ def test_absolute_and_relative_tolerance_modes():
 def test_exact_eigenspace_start_converges_at_pass_zero():
     """X0 spanning the exact eigenspace of the m smallest eigenvalues: every residual is at the
     rounding level at pass k = 0, so the loop exits there with iters = 0 and the closed-form
-    eigenvalues (the exit test of steps 7-8, reading R11)."""
+    eigenvalues (the exit test of the residuals and the soft-locking test, reading R11)."""
     dims = (5, 6, 7)                               # distinct axes: the smallest eigenvalues are simple
     A = L.Laplace7(dims)
     modes = laplace.exact_modes(dims, A.scale, 3)
@@ -223,7 +223,7 @@ def test_maxit_zero_only_checks_the_start():
     X0 = rng.uniform_block(2, A.n, 3)
     r = L.lobpcg(A, X0, 1e-8, 0)
     assert r.status == "not_converged" and r.iters == 0
-    # the result is the Rayleigh-Ritz of the start (steps 3-5): orthonormal X, Ritz values of span(X0)
+    # the result is the Rayleigh-Ritz of the start (the set-up): orthonormal X, Ritz values of span(X0)
     assert np.max(np.abs(r.X.T @ r.X - np.eye(3))) < 1e-12
     Q, _ = np.linalg.qr(X0)
     H = Q.T @ A(Q)
