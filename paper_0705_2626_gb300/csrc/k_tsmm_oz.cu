@@ -1,6 +1,6 @@
 // Float64 products of a tall block and a small coefficient matrix, Y = S C, on the tensor cores
-// by error-free digit products: the Ritz update of Algorithm steps 25-33 (X <- [X W P] C_X,
-// P <- [W P] C_P, and the A-side) and the triangular applies V <- V R^-1 of steps 3, 11 and
+// by error-free digit products: the Ritz update of the Ritz update (Section 2.2) (X <- [X W P] C_X,
+// P <- [W P] C_P, and the A-side) and the triangular applies V <- V R^-1 of the orthonormalisations of X and W and
 // 14-15, in the float64 form.
 //
 // Each grid point p (a row of S, at most 32 columns; column k scaled by an exact power of two
@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "common.cuh"
 #include "oz_digits.cuh"
@@ -140,6 +141,16 @@ __device__ __forceinline__ void tz_ld4(uint32_t taddr, float (&r)[4]) {
     r[3] = __uint_as_float(u3);
 }
 __device__ __forceinline__ void tz_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tz_ld8(uint32_t taddr, float (&r)[8]) {
+    uint32_t u[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = __uint_as_float(u[i]);
+}
 
 // Biased exponent field of x (0 for zeros and subnormals, 2047 for infinities and NaNs).
 __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
@@ -174,13 +185,18 @@ __device__ __forceinline__ double scaled_to_double(long long t, int ex) {
 // (the 14 bits rounded off lie 2^-57 below max |S(p, .)| max |C(., j)|; rounding to nearest
 // rather than down keeps the outputs free of a common bias).  ex = E_p + F_j - 56.
 __device__ __forceinline__ double combine_levels(const float (&D)[kTzLevels], int ex) {
-    int i[kTzLevels];
+    // b_L = bits of D_L + 1.5 2^23 = 0x4B400000 + D_L exactly (|D_L| < 2^22); the bias is taken
+    // out of each combination at once (32-bit wrap-around: every combination fits in 32 bits)
+    constexpr unsigned kB = 0x4B400000u;
+    unsigned b[kTzLevels];
 #pragma unroll
-    for (int L = 0; L < kTzLevels; ++L) i[L] = __float_as_int(D[L] + 12582912.0f) - 0x4B400000;
-    const int lo14 = i[5] * 128 + i[6] + ((i[7] * 128 + i[8] + 8192) >> 14);   // floor(x + 1/2)
-    const int a1 = i[0] * 128 + i[1];
-    const int a2 = i[2] * 128 + i[3];
-    const long long t = (long long)a1 * (1ll << 35) + (long long)a2 * (1ll << 21) + (long long)i[4] * (1ll << 14) +
+    for (int L = 0; L < kTzLevels; ++L) b[L] = __float_as_uint(D[L] + 12582912.0f);
+    const int lo14 = (int)(b[5] * 128u + b[6] - 129u * kB) +
+                     ((int)(b[7] * 128u + b[8] + (8192u - 129u * kB)) >> 14);   // floor(x + 1/2)
+    const int a1 = (int)(b[0] * 128u + b[1] - 129u * kB);
+    const int a2 = (int)(b[2] * 128u + b[3] - 129u * kB);
+    const int i4 = (int)(b[4] - kB);
+    const long long t = (long long)a1 * (1ll << 35) + (long long)a2 * (1ll << 21) + (long long)i4 * (1ll << 14) +
                         (long long)lo14;
     return scaled_to_double(t, ex);
 }
@@ -361,14 +377,18 @@ __global__ void __launch_bounds__(kTzThreads, 1) k_tsmm_oz(const __grid_constant
             const int em = ep[(t % kTzEpRing) * kTzTile + p];
             const int64_t P = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * kTzTile + p;
             const bool valid = P < a.n;
-#pragma unroll 1
-            for (int c = 0; c < a.nj; c += 4) {
-                float v[kTzLevels][4];
+            // outputs c .. c + W - 1 from their nine levels
+            auto drain = [&](int c, auto width) {
+                constexpr int W = decltype(width)::value;
+                float v[kTzLevels][W];
 #pragma unroll
-                for (int L = 0; L < kTzLevels; ++L) tz_ld4(tbase + (uint32_t)(L * a.nj + c), v[L]);
+                for (int L = 0; L < kTzLevels; ++L) {
+                    if constexpr (W == 8) tz_ld8(tbase + (uint32_t)(L * a.nj + c), v[L]);
+                    else tz_ld4(tbase + (uint32_t)(L * a.nj + c), v[L]);
+                }
                 tz_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < W; ++u) {
                     const int j = c + u;
                     if (j >= a.nout || !valid) continue;
                     float D[kTzLevels];
@@ -380,7 +400,14 @@ __global__ void __launch_bounds__(kTzThreads, 1) k_tsmm_oz(const __grid_constant
                     double* dst = j < a.nx ? a.out0 + (int64_t)j * a.ldout : a.out1 + (int64_t)(j - a.nx) * a.ldout;
                     dst[P] = y;
                 }
+            };
+            int c = 0;
+            if ((a.nj & 7) == 0) {         // 8-column loads stay 8-aligned in every level
+#pragma unroll 1
+                for (; c < a.nj; c += 8) drain(c, std::integral_constant<int, 8>());
             }
+#pragma unroll 1
+            for (; c < a.nj; c += 4) drain(c, std::integral_constant<int, 4>());
             tz_fence_before();
             __syncwarp();
             if (lane == 0) tz_arrive(&accempty[g]);
