@@ -73,6 +73,11 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 NCU_TRAFFIC = {("c4", "30669eedf80ddda4"): (536.889600e6 + 3.006976e6 + 537.195776e6 + 2.186752e6) * (24 / 16) *
                99897344 / 2097152}
 
+# DRAM traffic of one update launch of k_tsmm_oz (the Ritz update, 3m columns in, 2m out), from one
+# ncu capture of the same launch on the 128^3 grid scaled by the points to the workload, keyed by
+# the SHA-256 of k_tsmm_oz.cu and oz_digits.cuh (traffic = null after an edit of either).
+NCU_TRAFFIC_UPDATE = {}
+
 
 def closed_form_eigenvalues(dims, scale, m):
     """The m smallest eigenvalues of the scaled 7-point Dirichlet Laplacian, scale * sum over the
@@ -160,6 +165,20 @@ def gram_bytes_per_launch(n, m):
     """Compulsory bytes of the Gram matrices of the Rayleigh-Ritz basis at b = m: the float64 blocks [X W P] and [AX AW AP]
     (q = 3m columns each) read once, (2m + 4b) * 8 bytes per point."""
     return 2.0 * 3 * m * 8 * n
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_0705_2626_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def update_bytes_per_launch(n, m):
+    """Compulsory bytes of one update launch (the Ritz update, Section 2.2) at b = m: the 3m input
+    columns read once, the 2m outputs (X and P, or AX and AP) written once, 8 bytes each."""
+    return (3 * m + 2 * m) * 8.0 * n
 
 
 def kernel_source_hash():
@@ -393,6 +412,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = gram_bytes_per_launch(n, m) / (gram_ms * 1e-3) / 1e9
     fp64_equiv = gram_flops_per_launch(n, m) / (gram_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get((w, kernel_source_hash()))
+    upd_launch_ms = ph64["update"] / 2                 # the update phase is two launches of k_tsmm_oz
+    upd_achieved = update_bytes_per_launch(n, m) / (upd_launch_ms * 1e-3) / 1e9
+    upd_traffic = NCU_TRAFFIC_UPDATE.get((w, source_hash("k_tsmm_oz.cu", "oz_digits.cuh")))
     out64, ttt64 = time_to_tol(s64)
 
     # ---- end to end through the public API with host buffers (float64 form): X0 from pinned
@@ -466,11 +488,19 @@ def run_ours(args, rank, world, local_rank):
                          fp64=ttt_brief(ttt64, out64), mixed=ttt_brief(tttmx, outmx),
                          mixed_speedup=rnd(ttt64["time_to_tol_s"] / tttmx["time_to_tol_s"], 3),
                          max_rel_lambda_diff_mixed_vs_fp64=rnd(lam_diff, 2)),
-        roofline=dict(kernel="Gram phase, the Gram matrices of the Rayleigh-Ritz basis: k_oz_exponents + k_gram_oz + k_gram_finalize (float64 "
-                             "Gram by bfloat16 digit products on the tensor cores)", bound="hbm",
-                      achieved=achieved, peak=HBM_PEAK_GBS, unit="GB/s", frac=achieved / HBM_PEAK_GBS,
-                      traffic=traffic, algorithmic_bytes=gram_bytes_per_launch(n, m), peak_source=HBM_PEAK_SOURCE,
-                      fp64_equiv_tflops=fp64_equiv, fp64_pipe_tflops=FP64_PEAK_TFLOPS),
+        roofline=dict(kernel="k_tsmm_oz, one update launch (the Ritz update, Section 2.2: float64 [X W P] C or "
+                             "[AX AW AP] C by bfloat16 digit products on the tensor cores; the top kernel of the "
+                             "launch list)", bound="hbm",
+                      achieved=upd_achieved, peak=HBM_PEAK_GBS, unit="GB/s", frac=upd_achieved / HBM_PEAK_GBS,
+                      traffic=upd_traffic, algorithmic_bytes=update_bytes_per_launch(n, m),
+                      launch_ms=upd_launch_ms, peak_source=HBM_PEAK_SOURCE),
+        roofline_gram=dict(kernel="Gram phase, the Gram matrices of the Rayleigh-Ritz basis: k_oz_exponents + "
+                                  "k_gram_oz + k_gram_finalize (float64 Gram by bfloat16 digit products on the "
+                                  "tensor cores)", bound="hbm",
+                           achieved=achieved, peak=HBM_PEAK_GBS, unit="GB/s", frac=achieved / HBM_PEAK_GBS,
+                           traffic=traffic, algorithmic_bytes=gram_bytes_per_launch(n, m),
+                           peak_source=HBM_PEAK_SOURCE, fp64_equiv_tflops=fp64_equiv,
+                           fp64_pipe_tflops=FP64_PEAK_TFLOPS),
         mixed=dict(value=replica_throughput(args.steps, world, tmx), unit="iters/s", ms_per_step=tmx / args.steps,
                    dtype="f64+f32+bf16", gpu_launches=launches_mx,
                    phase_ms=dict((k, rnd(v)) for k, v in phmx.items()), hbm_frac=kernmx),
