@@ -74,9 +74,12 @@ NCU_TRAFFIC = {("c4", "30669eedf80ddda4"): (536.889600e6 + 3.006976e6 + 537.1957
                99897344 / 2097152}
 
 # DRAM traffic of one update launch of k_tsmm_oz (the Ritz update, 3m columns in, 2m out), from one
-# ncu capture of the same launch on the 128^3 grid scaled by the points to the workload, keyed by
-# the SHA-256 of k_tsmm_oz.cu and oz_digits.cuh (traffic = null after an edit of either).
-NCU_TRAFFIC_UPDATE = {}
+# ncu capture of the same launches on the 128^3 grid (mean of the X-side and A-side launch: read +
+# write; up to ~50 MB of the writes were still in L2 at the end of the small launch) scaled by the
+# points to the workload, keyed by the SHA-256 of k_tsmm_oz.cu and oz_digits.cuh (traffic = null
+# after an edit of either).
+NCU_TRAFFIC_UPDATE = {("c4", "006a3531d28af7fb"): ((402.728960e6 + 402.815488e6) / 2 + (215.070976e6 + 211.512832e6) / 2) *
+                      99897344 / 2097152}
 
 
 def closed_form_eigenvalues(dims, scale, m):
