@@ -1,5 +1,5 @@
-// Float64 Gram matrices on the tensor cores (Section 2.2, and the Cholesky Grams of
-// the orthonormalisations of X, W and P, in the float64 form) by error-free digit products.
+// Float64 Gram matrices of the Rayleigh-Ritz basis on the tensor cores (Section 2.2, the float64
+// form) by error-free digit products.
 //
 // GB300 runs float64 fused multiply-adds at 2 per clock per SM; its bfloat16 tensor cores are
 // about three orders of magnitude faster.  Within a window of kOzWindow grid points every
