@@ -86,3 +86,21 @@ def test_cpu_sample_scaling():
     assert "scaled" in text and "m=8" in text
     key, _, factor, _ = bench.cpu_sample_desc("c1")
     assert key == "c1" and factor == 1.0
+
+
+def test_roofline_bytes_and_traffic_keys():
+    """The algorithmic bytes of the two roofline lines, and the source hashes their recorded DRAM
+    traffic is keyed to (an edit of the kernel source must drop the recorded traffic)."""
+    n, m = 1000, 8
+    assert bench.update_bytes_per_launch(n, m) == (3 * m + 2 * m) * 8 * n       # 3m read, 2m written
+    assert bench.gram_bytes_per_launch(n, m) == 2 * 3 * m * 8 * n               # [S AS] read once
+    h = bench.source_hash("k_tsmm_oz.cu", "oz_digits.cuh")
+    assert len(h) == 16 and h == bench.source_hash("k_tsmm_oz.cu", "oz_digits.cuh")
+    assert h != bench.source_hash("k_gram_oz.cu", "oz_digits.cuh")
+    assert bench.kernel_source_hash() == bench.source_hash("k_gram_oz.cu", "oz_digits.cuh")
+    # the recorded traffic is per launch / per iteration of the 464^3 workload, near the algorithmic bytes
+    n4 = 464 ** 3
+    for (w, key), t in bench.NCU_TRAFFIC_UPDATE.items():
+        assert w == "c4" and 0.8 < t / bench.update_bytes_per_launch(n4, 8) < 1.2
+    for (w, key), t in bench.NCU_TRAFFIC.items():
+        assert w == "c4" and 1.5 < t / bench.gram_bytes_per_launch(n4, 8) < 2.5
