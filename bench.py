@@ -79,7 +79,7 @@ NCU_TRAFFIC = {("c4", "bd214596424a0ec6"): (536.889600e6 + 3.006976e6 + 537.1957
 # write; up to ~50 MB of the writes were still in L2 at the end of the small launch) scaled by the
 # points to the workload, keyed by the SHA-256 of k_tsmm_oz.cu and oz_digits.cuh (traffic = null
 # after an edit of either).
-NCU_TRAFFIC_UPDATE = {("c4", "006a3531d28af7fb"): ((402.728960e6 + 402.815488e6) / 2 + (215.070976e6 + 211.512832e6) / 2) *
+NCU_TRAFFIC_UPDATE = {("c4", "e790013c613854da"): ((402.801920e6 + 402.797824e6) / 2 + (216.686080e6 + 215.953664e6) / 2) *
                       99897344 / 2097152}
 
 

@@ -163,21 +163,19 @@ __device__ __forceinline__ uint4 digits8(double x, int emax) {
     return make_uint4(oz_pack2(d[0], d[1]), oz_pack2(d[2], d[3]), oz_pack2(d[4], d[5]), oz_pack2(d[6], d[7]));
 }
 
-// t 2^ex rounded to float64 (nearest, ties to even) by integer operations only, without branches;
-// results below the normal range are flushed to zero.
+// t 2^ex rounded to float64 (nearest, ties to even): the conversion of t is the one rounding
+// (on the otherwise idle float64 pipe), the power of two is added to the exponent field; results
+// below the normal range are flushed to zero, results above it become infinities.
 __device__ __forceinline__ double scaled_to_double(long long t, int ex) {
-    const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
-    const unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
-    const int lz = __clzll((long long)(a | 1ull));
-    const unsigned long long top = a << lz;            // leading one at bit 63 (t != 0)
-    const unsigned long long rest = top & 0x7FFull;
-    unsigned long long mant = top >> 11;               // 53 bits, leading one at bit 52
-    mant += (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
-    const int eb = 63 - lz + ex + 1023;                // biased exponent of the leading one
-    unsigned long long bits = sgn | (((unsigned long long)(eb - 1) << 52) + mant);
-    bits = eb >= 2047 ? (sgn | 0x7FF0000000000000ull) : bits;
-    bits = (eb <= 0 || t == 0) ? sgn : bits;
-    return __longlong_as_double((long long)bits);
+    const double y = __ll2double_rn(t);
+    const int hi = __double2hiint(y), lo = __double2loint(y);
+    const int e = ((hi >> 20) & 0x7FF) + ex;           // biased exponent of the result
+    const int sgn = hi & (int)0x80000000u;
+    const bool over = e >= 2047, under = e <= 0 || t == 0;
+    int rh = hi + (int)((unsigned)ex << 20);
+    rh = over ? (sgn | 0x7FF00000) : rh;
+    rh = under ? sgn : rh;
+    return __hiloint2double(rh, (over || under) ? 0 : lo);
 }
 
 // One output from its nine levels D_0..D_8 (exact float32 integers, |D| < 2^22):
