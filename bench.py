@@ -70,8 +70,8 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm()
 # ncu capture on the 128^3 grid (its first-iteration Gram, q = 16 columns: read + write of both
 # launches) scaled by the columns (24 / 16) and the points (464^3 / 128^3) to the workload, keyed
 # by the SHA-256 of k_gram_oz.cu and oz_digits.cuh; a changed source invalidates it (traffic = null;
-# the key was renewed once after an edit of comments only).
-NCU_TRAFFIC = {("c4", "bd214596424a0ec6"): (536.889600e6 + 3.006976e6 + 537.195776e6 + 2.186752e6) * (24 / 16) *
+# the key was renewed twice, after edits of comments only).
+NCU_TRAFFIC = {("c4", "3591edfac0184e1b"): (536.889600e6 + 3.006976e6 + 537.195776e6 + 2.186752e6) * (24 / 16) *
                99897344 / 2097152}
 
 # DRAM traffic of one update launch of k_tsmm_oz (the Ritz update, 3m columns in, 2m out), from one

@@ -15,12 +15,13 @@
 // exactly, one TMEM accumulator per pair, over a window of 1024 points.  The window's share of
 // the entry,
 //     sum_p x_i y_j = 2^(E_i + E_j - 112) sum_{s,t} D_st 2^(7 (14 - s - t)),
-// is formed in 64-bit integer arithmetic (exact down to 2^-60 of its largest possible value) and
-// added to a float64 total per entry.  This is the splitting method of Ozaki, Ogita and Oishi
-// ("Error-free transformations of matrix multiplication by using fast routines of matrix
-// multiplication and its applications", Numer. Algorithms 59, 2012) with a common exponent per
-// column and window and every digit pair kept: the per-window result carries about 2^-56 of the
-// window's largest products, below the rounding of a float64 dot product.
+// is formed in 64-bit integer arithmetic (truncated at 2^-62 of its largest possible value); the
+// shares of the 16 windows of one exponent window are summed exactly in 128-bit integers and
+// added, converted to float64 once, to the entry's float64 total.  This is the splitting method
+// of Ozaki, Ogita and Oishi ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms 59, 2012) with a
+// common exponent per column and window and every digit pair kept: the per-window result carries
+// about 2^-56 of the window's largest products, below the rounding of a float64 dot product.
 //
 // Operands (the K dimension is the grid point): A = the digit lines of the left block L = S, line
 // 8 i + s = digit s of column i (M = 128 lines per tile, up to 3 tiles); B = the digit lines of a
