@@ -11,7 +11,10 @@ This file computes the same scheme in numpy integers, independently of the CUDA 
 checks that the bound holds with a margin for the model itself (so the GPU tests do not pass by a
 loose tolerance), that it is not vacuous (the model's error does reach a fair part of it on
 full-mantissa inputs), and that every level sum stays below 2^22, which keeps the tensor cores'
-float32 sums exact for q <= 32.
+float32 sums exact for q <= 32.  The second part does the same for the tensor-core float64 Gram
+(windowed frames, every digit pair kept, truncated integer combination): its error stays inside
+the bound derived from those steps, far inside the 2 n eps bar of the GPU Gram tests, and within
+one eps of sum_p |x_i(p)| |y_j(p)| on grid functions and on random columns.
 """
 import numpy as np
 import pytest
@@ -131,3 +134,96 @@ def test_digits_reassemble_to_the_rounded_value():
     exact = np.ldexp(x.astype(np.longdouble), 56 - E)                    # x 2^(56 - E), exact
     assert np.all(np.abs(F.astype(np.longdouble) - exact) <= 0.5)
     assert np.all(np.abs(d) <= 127) and np.all(F[::50] == 0)
+
+
+# ---------------------------------------------------------------- the float64 Gram (tensor cores)
+# Per column and exponent window of 16384 points the frame is the column's largest exponent field
+# there; per accumulation window of 1024 points every digit-pair sum D_st(i, j) is exact; line s
+# of column i contributes hi 2^(17 - 7 s) + lo 2^(-11 - 7 s) (each shift a floor) with
+# hi = sum_{t<4} D_st 2^(7 (3 - t)) and lo = sum_{t>=4} D_st 2^(7 (7 - t)), in units of
+# 2^(E_i + E_j - 52); the windows of one exponent window are summed exactly, converted to
+# float64 once and added to the entry.
+
+EXP_PTS, WIN_PTS = 16384, 1024
+
+
+def gram_model(L, R):
+    n, qa = L.shape
+    qb = R.shape[1]
+    G = np.zeros((qa, qb))
+    parts = []
+    for e0 in range(0, n, EXP_PTS):
+        Le, Re = L[e0:e0 + EXP_PTS], R[e0:e0 + EXP_PTS]
+        ei, ej = exponent_field(Le).max(axis=0), exponent_field(Re).max(axis=0)
+        dL, dR = digits(Le, ei[None, :]), digits(Re, ej[None, :])
+        acc = np.zeros((qa, qb), dtype=object)
+        for w0 in range(0, Le.shape[0], WIN_PTS):
+            D = np.einsum("pis,pjt->isjt", dL[w0:w0 + WIN_PTS], dR[w0:w0 + WIN_PTS])    # exact int64
+            assert np.max(np.abs(D)) < 2 ** 24
+            c = np.zeros((qa, qb), dtype=np.int64)
+            for s in range(8):
+                hi = sum(D[:, s, :, t] * (1 << (7 * (3 - t))) for t in range(4))
+                lo = sum(D[:, s, :, t] * (1 << (7 * (7 - t))) for t in range(4, 8))
+                shl = 17 - 7 * s
+                c += (hi << shl) if shl >= 0 else (hi >> -shl)
+                c += lo >> (11 + 7 * s)
+            acc = acc + c.astype(object)
+        part = np.array([[np.ldexp(float(acc[i, j]), int(ei[i] + ej[j] - 2096)) for j in range(qb)]
+                         for i in range(qa)])
+        parts.append((part, ei, ej, Le, Re))
+        G += part
+    return G, parts
+
+
+def gram_model_bound(parts):
+    """Digit rounding (2^(E - 57) per element against the other column's absolute sum), the
+    dropped products of two rounding errors, the truncation (at most 16 units per window), and the
+    float64 conversions and additions of the exponent windows' parts."""
+    tot, absparts = 0.0, 0.0
+    k = len(parts)
+    for part, ei, ej, Le, Re in parts:
+        Ei, Ej = ei.astype(float) - 1022, ej.astype(float) - 1022
+        sx, sy = np.abs(Le).sum(axis=0), np.abs(Re).sum(axis=0)
+        nw = -(-Le.shape[0] // WIN_PTS)
+        scale = np.ldexp(1.0, (Ei[:, None] + Ej[None, :]).astype(int))
+        tot = tot + np.ldexp(1.0, (Ei - 57).astype(int))[:, None] * sy[None, :] + \
+            np.ldexp(1.0, (Ej - 57).astype(int))[None, :] * sx[:, None] + \
+            scale * (2.0 ** -114 * Le.shape[0] + 16 * nw * 2.0 ** -52)
+        absparts = absparts + np.abs(part)
+    return tot + (k + 1) * 2.0 ** -53 * absparts
+
+
+def grid_columns(nx, ny, nz, q, seed):
+    """Sine modes with noise, each column at its own scale: the kind of basis LOBPCG builds."""
+    g = np.random.default_rng(seed)
+    ii, jj, kk = np.meshgrid(np.arange(1, nx + 1), np.arange(1, ny + 1), np.arange(1, nz + 1), indexing="ij")
+    cols = []
+    for c in range(q):
+        a, b, d = 1 + c % 3, 1 + (c // 3) % 3, 1 + c // 9
+        f = np.sin(a * np.pi * ii / (nx + 1)) * np.sin(b * np.pi * jj / (ny + 1)) * np.sin(d * np.pi * kk / (nz + 1))
+        cols.append(f.transpose(2, 1, 0).ravel() * 10.0 ** g.uniform(-3, 3) + 1e-5 * g.standard_normal(f.size))
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("kind", ["grid", "random"])
+def test_gram_model_within_its_bound_and_the_float64_test_bound(kind):
+    if kind == "grid":
+        X = grid_columns(40, 36, 34, 12, 7)                    # 48,960 points: 3 exponent windows, ragged
+    else:
+        g = np.random.default_rng(8)
+        X = g.standard_normal((40000, 12)) * 10.0 ** g.uniform(-4, 4, 12)[None, :]
+        X[::97] = 0.0
+    L, R = X[:, :6], X
+    G, parts = gram_model(L, R)
+    want = L.astype(np.longdouble).T @ R.astype(np.longdouble)
+    err = np.abs(G.astype(np.longdouble) - want).astype(np.float64)
+    mb = gram_model_bound(parts)
+    assert np.all(err <= mb), float(np.max(err / mb))
+    n = X.shape[0]
+    eps = np.finfo(np.float64).eps
+    gpu_bound = 2 * n * eps * np.outer(np.linalg.norm(L, axis=0), np.linalg.norm(R, axis=0))
+    assert np.all(mb <= 1e-3 * gpu_bound)                      # far inside the GPU test's bar
+    # float64 quality: on these bases the scheme stays within one eps of sum_p |x_i| |y_j| (the
+    # float64 product L^T R in numpy reaches about 2 eps on the same data)
+    absdot = np.abs(L).T @ np.abs(R)
+    assert np.all(err <= eps * absdot), float(np.max(err / (eps * absdot)))
